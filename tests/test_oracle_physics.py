@@ -1,0 +1,255 @@
+"""Pins of the oracle's cross sections and stopping powers against what the definitions
+fix: numerical integrals of the differential cross sections (scipy quad), limits and
+symmetries of those differentials, independent unrestricted stopping-power forms,
+high-precision (mpmath) evaluations, and PDG radiation lengths.
+
+The paper names the physics library only (G4HepEm, Sec. 2.2); the models are the
+textbook forms listed in the oracle's header.
+"""
+import math
+
+import mpmath
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from paper_2209_15445_gb300 import workloads as w
+
+ME = 0.51099895
+RE = 2.8179403262e-12
+ALPHA = 1 / 137.035999084
+NA = 6.02214076e23
+PB, LAR = 0, 1
+
+
+def n_el(mat):
+    return NA * mat.density / mat.A * 1e-3 * mat.Z
+
+
+def quad(f, a, b, **kw):
+    v, err = integrate.quad(f, a, b, epsabs=0.0, epsrel=1e-12, limit=400, **kw)
+    return v
+
+
+def logquad(f, a, b):
+    """integral of f over [a, b] (a > 0) in the variable ln x, for 1/x^2-like integrands"""
+    return quad(lambda t: f(math.exp(t)) * math.exp(t), math.log(a), math.log(b))
+
+
+# ---------------------------------------------------------------- Compton
+def kn_dsig_deps(eps, kap):
+    """Klein-Nishina per electron written in eps = E'/E from dsigma/dOmega =
+    re^2/2 eps^2 (eps + 1/eps - sin^2 theta), cos theta = 1 - (1/eps - 1)/kappa."""
+    c = 1 - (1 / eps - 1) / kap
+    return math.pi * RE**2 / kap * (eps + 1 / eps - (1 - c * c))
+
+
+@pytest.mark.parametrize("E", [0.002, 0.05, 0.3, 1.0, 10.0, 1e3, 1e5])
+def test_compton_total_is_integral_of_differential(E):
+    kap = E / ME
+    e0 = 1 / (1 + 2 * kap)
+    ref = quad(lambda e: kn_dsig_deps(e, kap), e0, 1.0, points=[e0 * 2] if e0 * 2 < 1 else None)
+    got = oracle.lib().or_sigma_kn(kap)
+    assert got == pytest.approx(ref, rel=1e-9)
+
+
+def test_compton_series_matches_high_precision_closed_form():
+    mpmath.mp.dps = 50
+    for k in [1e-6, 1e-4, 3e-3, 0.01, 0.0199, 0.02, 0.05, 0.3]:
+        K = mpmath.mpf(k)
+        l = mpmath.log(1 + 2 * K)
+        b = (1 + K) / K**2 * (2 * (1 + K) / (1 + 2 * K) - l / K) + l / (2 * K) - (1 + 3 * K) / (1 + 2 * K) ** 2
+        ref = float(2 * mpmath.pi * mpmath.mpf(RE) ** 2 * b)
+        assert oracle.lib().or_sigma_kn(k) == pytest.approx(ref, rel=2e-15)
+    # the unexpanded form agrees with the series where both are accurate
+    for k in [0.02, 0.03, 0.05]:
+        assert oracle.lib().or_sigma_kn_direct(k) == pytest.approx(oracle.lib().or_sigma_kn(k), rel=1e-13)
+
+
+def test_compton_limits():
+    sth = 8 * math.pi / 3 * RE**2
+    assert oracle.lib().or_sigma_kn(1e-9) == pytest.approx(sth, rel=1e-8)  # Thomson limit
+    k = 1e5  # high-energy limit pi re^2 / k (ln 2k + 1/2)
+    assert oracle.lib().or_sigma_kn(k) == pytest.approx(math.pi * RE**2 / k * (math.log(2 * k) + 0.5), rel=1e-4)
+
+
+def test_compton_mu_scales_with_electron_density(slab_oracle):
+    mats = w.slab_calorimeter().materials
+    for E in (0.1, 1.0, 10.0):
+        ratio = slab_oracle.mu_compton(PB, E) / slab_oracle.mu_compton(LAR, E)
+        assert ratio == pytest.approx(n_el(mats[0]) / n_el(mats[1]), rel=1e-14)
+
+
+# ---------------------------------------------------------------- pair, X0, photo
+@pytest.mark.parametrize("mat,x0_gcm2", [(w.PB, 6.37), (w.LAR, 19.55), (w.FE, 13.84), (w.SI, 21.82)])
+def test_radiation_length_matches_pdg(mat, x0_gcm2):
+    g = w.Geometry(kind=0, n_layers=1, materials=[mat], sub_materials=[0], sub_thickness=[10.0], half_xy=100.0)
+    o = oracle.Oracle(g)
+    x0_mm = 1.0 / o.inv_X0(0)
+    assert x0_mm * mat.density / 10.0 == pytest.approx(x0_gcm2, rel=5e-3)
+
+
+@pytest.mark.parametrize("E", [1.05, 1.5, 3.0, 10.0, 100.0, 1e4, 1e6])
+def test_pair_total_is_integral_of_differential(slab_oracle, E):
+    a = ME / E
+    ix0 = slab_oracle.inv_X0(PB)
+    ref = quad(lambda x: ix0 * (1 - 4 / 3 * x * (1 - x)), a, 1 - a)
+    assert slab_oracle.mu_pair(PB, E) == pytest.approx(ref, rel=1e-12)
+
+
+def test_pair_threshold_and_asymptote(slab_oracle):
+    assert slab_oracle.mu_pair(PB, 2 * ME) == 0.0
+    assert slab_oracle.mu_pair(PB, 1.0) == 0.0
+    assert slab_oracle.mu_pair(PB, 1e9) == pytest.approx(7 / 9 * slab_oracle.inv_X0(PB), rel=1e-8)
+
+
+def test_photo_scaling(slab_oracle):
+    mats = w.slab_calorimeter().materials
+    for E in (0.01, 0.1, 1.0):
+        assert slab_oracle.mu_photo(PB, 2 * E) / slab_oracle.mu_photo(PB, E) == pytest.approx(2**-3.5, rel=1e-14)
+    nat = [NA * m.density / m.A for m in mats]
+    r = slab_oracle.mu_photo(PB, 0.1) / slab_oracle.mu_photo(LAR, 0.1)
+    assert r == pytest.approx((82 / 18) ** 5 * nat[0] / nat[1], rel=1e-13)
+    # Born K-shell magnitude for Pb at 100 keV: order 10^2 per cm (no edges, no screening)
+    assert 1e1 < slab_oracle.mu_photo(PB, 0.1) * 10 < 1e3
+
+
+# ---------------------------------------------------------------- ionisation
+def moller(eps, T):
+    g = T / ME + 1
+    b2 = 1 - 1 / g**2
+    gg = (2 * g - 1) / g**2
+    return 2 * math.pi * RE**2 * ME / (b2 * T) * ((1 - gg) + 1 / eps**2 + 1 / (1 - eps) ** 2 - gg / (eps * (1 - eps)))
+
+
+def bhabha(eps, T):
+    g = T / ME + 1
+    b2 = 1 - 1 / g**2
+    y = 1 / (g + 1)
+    y12 = 1 - 2 * y
+    B1, B2, B4 = 2 - y * y, y12 * (3 + y * y), y12**3
+    B3 = B4 + y12**2
+    return 2 * math.pi * RE**2 * ME / T * (1 / (b2 * eps**2) - B1 / eps + B2 - B3 * eps + B4 * eps**2)
+
+
+def test_moller_bhabha_differentials_limits():
+    T = 5.0
+    g = T / ME + 1
+    b2 = 1 - 1 / g**2
+    # Moller is symmetric under eps <-> 1 - eps (identical particles)
+    for e in (0.01, 0.1, 0.3):
+        assert moller(e, T) == pytest.approx(moller(1 - e, T), rel=1e-13)
+    # both tend to free-electron Rutherford scattering at small energy transfer
+    ruth = lambda e: 2 * math.pi * RE**2 * ME / (b2 * T * e * e)
+    assert moller(1e-6, T) == pytest.approx(ruth(1e-6), rel=1e-5)
+    assert bhabha(1e-6, T) == pytest.approx(ruth(1e-6), rel=1e-5)
+    # ultra-relativistic Bhabha: (1 - e + e^2)^2 / e^2 per 2 pi re^2 m / T
+    T = 1e7
+    for e in (0.1, 0.5, 0.9):
+        assert bhabha(e, T) / (2 * math.pi * RE**2 * ME / T) == pytest.approx((1 - e + e * e) ** 2 / e**2, rel=1e-6)
+
+
+@pytest.mark.parametrize("T", [0.01, 0.3, 2.0, 30.0, 1e3, 1e5])
+def test_ioni_totals_are_integrals_of_differentials(slab_oracle, T):
+    ne = n_el(w.PB)
+    for cut in (1e-3, 0.05, 1.0):
+        if T > 2 * cut:
+            ref = ne * logquad(lambda e: moller(e, T), cut / T, 0.5)
+            assert slab_oracle.lambda_ioni(PB, T, cut, 0) == pytest.approx(ref, rel=1e-9)
+        else:
+            assert slab_oracle.lambda_ioni(PB, T, cut, 0) == 0.0
+        if T > cut:
+            ref = ne * logquad(lambda e: bhabha(e, T), cut / T, 1.0)
+            assert slab_oracle.lambda_ioni(PB, T, cut, 1) == pytest.approx(ref, rel=1e-9)
+        else:
+            assert slab_oracle.lambda_ioni(PB, T, cut, 1) == 0.0
+
+
+@pytest.mark.parametrize("T", [0.05, 1.0, 20.0, 1e3])
+def test_restricted_loss_equals_unrestricted_minus_delta_rays(slab_oracle, T):
+    """S(cut1) - S(cut2) = n_el * integral of T_delta dsigma/dT_delta over [cut1, cut2]:
+    ties the Berger-Seltzer restricted forms to the Moller/Bhabha cross sections."""
+    ne = n_el(w.PB)
+    c1, c2 = 0.02 * T, 0.4 * T
+    ref = ne * quad(lambda e: e * T * moller(e, T), c1 / T, c2 / T)
+    d = slab_oracle.dedx_col(PB, T, c2, 0) - slab_oracle.dedx_col(PB, T, c1, 0)
+    assert d == pytest.approx(ref, rel=1e-8)
+    c2 = 0.9 * T
+    ref = ne * quad(lambda e: e * T * bhabha(e, T), c1 / T, c2 / T)
+    d = slab_oracle.dedx_col(PB, T, c2, 1) - slab_oracle.dedx_col(PB, T, c1, 1)
+    assert d == pytest.approx(ref, rel=1e-8)
+
+
+@pytest.mark.parametrize("T", [0.01, 0.2, 1.0, 10.0, 1e3])
+def test_unrestricted_collision_loss_matches_rohrlich_carlson(slab_oracle, T):
+    """At cut >= T/2 (e-) or T (e+) the restricted form must equal the textbook unrestricted
+    one: 2 pi re^2 m n_el / b2 [ln(tau^2(tau+2)/(2 (I/m)^2)) + F(tau) - delta] with
+    F- = 1 - b2 + [tau^2/8 - (2 tau + 1) ln 2]/(tau+1)^2 and
+    F+ = 2 ln 2 - b2/12 [23 + 14/(tau+2) + 10/(tau+2)^2 + 4/(tau+2)^3]."""
+    tau = T / ME
+    b2 = tau * (tau + 2) / (tau + 1) ** 2
+    Im = w.PB.I_eV * 1e-6 / ME
+    base = math.log(tau**2 * (tau + 2) / (2 * Im**2)) - slab_oracle.delta(PB, T)
+    Fm = 1 - b2 + (tau**2 / 8 - (2 * tau + 1) * math.log(2)) / (tau + 1) ** 2
+    Fp = 2 * math.log(2) - b2 / 12 * (23 + 14 / (tau + 2) + 10 / (tau + 2) ** 2 + 4 / (tau + 2) ** 3)
+    k = 2 * math.pi * RE**2 * ME * n_el(w.PB) / b2
+    assert slab_oracle.dedx_col(PB, T, 10 * T, 0) == pytest.approx(k * (base + Fm), rel=1e-11)
+    assert slab_oracle.dedx_col(PB, T, 10 * T, 1) == pytest.approx(k * (base + Fp), rel=1e-11)
+
+
+def test_collision_loss_sanity_range(slab_oracle):
+    # electrons in Pb at 1 MeV lose ~1 MeV cm^2/g by collisions (ESTAR-like magnitude)
+    assert 0.85 < slab_oracle.dedx_col(PB, 1.0, 1.0, 0) * 10 / w.PB.density < 1.15
+    assert 1.2 < slab_oracle.dedx_col(LAR, 1.0, 1.0, 0) * 10 / w.LAR.density < 1.6
+
+
+def test_density_effect_continuity_and_asymptote(slab_oracle):
+    # delta is continuous (and 0 below x0); at high energy 2 ln(10) x - Cbar with
+    # Cbar = 2 ln(I / hbar omega_p) + 1, hbar omega_p = 28.816 sqrt(rho Z/A) eV
+    hwp = 28.816 * math.sqrt(w.PB.density * w.PB.Z / w.PB.A)
+    cbar = 2 * math.log(w.PB.I_eV / hwp) + 1
+    assert cbar == pytest.approx(6.2018, rel=1e-3)  # Sternheimer's tabulated -C for Pb
+    T = 1e5
+    x = math.log10(math.sqrt(T / ME * (T / ME + 2)))
+    assert slab_oracle.delta(PB, T) == pytest.approx(2 * math.log(10) * x - cbar, rel=1e-12)
+    Ts = np.exp(np.linspace(np.log(1e-3), np.log(1e6), 20000))
+    d = np.array([slab_oracle.delta(PB, t) for t in Ts])
+    assert np.all(np.diff(d) >= -1e-12)
+    assert np.max(np.abs(np.diff(d))) < 0.01
+    assert d[0] == 0.0
+
+
+# ---------------------------------------------------------------- bremsstrahlung, annihilation
+@pytest.mark.parametrize("T", [0.02, 1.0, 50.0, 1e4])
+def test_brem_total_and_restricted_loss_are_integrals(slab_oracle, T):
+    ix0 = slab_oracle.inv_X0(PB)
+    E = T + ME
+    f = lambda k: ix0 * (4 / 3 - 4 / 3 * (k / E) + (k / E) ** 2) / k
+    for kc in (1e-3, 0.1, 5.0):
+        if T > kc:
+            assert slab_oracle.lambda_brem(PB, T, kc) == pytest.approx(logquad(f, kc, T), rel=1e-10)
+        else:
+            assert slab_oracle.lambda_brem(PB, T, kc) == 0.0
+        kk = min(kc, T)
+        assert slab_oracle.dedx_rad(PB, T, kc) == pytest.approx(quad(lambda k: k * f(k), 0.0, kk), rel=1e-12)
+
+
+def heitler(eps, T):
+    g = T / ME + 1
+    S = lambda e: -(g + 1) ** 2 + (g * g + 4 * g + 1) / e - 1 / e**2
+    return math.pi * RE**2 / ((g + 1) * (g * g - 1)) * (S(eps) + S(1 - eps))
+
+
+@pytest.mark.parametrize("T", [0.002, 0.1, 1.0, 100.0, 1e5])
+def test_annihilation_total_is_integral_of_differential(slab_oracle, T):
+    g = T / ME + 1
+    sq = math.sqrt((g - 1) / (g + 1))
+    emin, emax = (1 - sq) / 2, (1 + sq) / 2
+    # each annihilation gives two photons: the integral over both counts every event twice
+    ref = 0.5 * n_el(w.PB) * quad(lambda e: heitler(e, T), emin, emax)
+    assert slab_oracle.lambda_annih(PB, T) == pytest.approx(ref, rel=1e-9)
+    # Dirac's low-energy limit: sigma -> pi re^2 / beta
+    b = math.sqrt(1 - 1 / g**2)
+    if T < 0.003:
+        assert slab_oracle.lambda_annih(PB, T) / n_el(w.PB) == pytest.approx(math.pi * RE**2 / b, rel=0.01)
