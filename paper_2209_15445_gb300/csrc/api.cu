@@ -1,0 +1,866 @@
+// Host runtime behind the C ABI (include/adept.h): argument checking, the arena layout,
+// request buffering and admission, the generation loop with CUDA graphs, completion
+// tracking and result return. Every physics step runs in the kernels of kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/adept.h"
+#include "layout.h"
+
+using namespace adept;
+
+static_assert(sizeof(adept_track) == sizeof(TrackIn), "adept_track layout");
+static_assert(offsetof(adept_track, E_kin_MeV) == offsetof(TrackIn, E), "adept_track layout");
+static_assert(offsetof(adept_track, pos_mm) == offsetof(TrackIn, pos), "adept_track layout");
+static_assert(offsetof(adept_track, dir) == offsetof(TrackIn, dir), "adept_track layout");
+static_assert(offsetof(adept_track, event) == offsetof(TrackIn, event), "adept_track layout");
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+constexpr uint32_t kDoneChunk = 4096;  // done-list entries copied back with each status read
+
+struct Request {
+  uint32_t id = 0;
+  size_t n = 0;
+  std::vector<adept_track> host;       // host submission (copied)
+  const adept_track* dev = nullptr;    // device submission (caller-owned)
+  std::vector<uint32_t> meta;          // [event index, track id] per track
+  std::vector<uint32_t> keys;          // RNG key (caller's event number) per event
+  double energy = 0.0;                 // primary energy incl. 2 m for positrons
+  uint32_t slot_base = 0;
+  uint32_t remaining = 0;              // events not finished
+  int state = 0;                       // 0 pending, 1 in flight, 2 done
+  Clock::time_point t_submit, t_done;
+  std::vector<double> edep, leaked, killed;
+};
+
+struct SlotAlloc {  // first-fit allocator of contiguous event-slot ranges
+  std::map<uint32_t, uint32_t> free_;  // start -> length
+  void init(uint32_t n) { free_.clear(); if (n) free_[0] = n; }
+  bool alloc(uint32_t n, uint32_t* out) {
+    if (n == 0) { *out = 0; return true; }
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *out = it->first;
+        const uint32_t s = it->first + n, l = it->second - n;
+        free_.erase(it);
+        if (l) free_[s] = l;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint32_t s, uint32_t n) {
+    if (!n) return;
+    auto it = free_.emplace(s, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) { it->second += nx->second; free_.erase(nx); }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) { pv->second += it->second; free_.erase(it); }
+    }
+  }
+};
+
+}  // namespace
+
+struct adept_ctx {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  adept_options opt{};
+  int n_mat = 0;
+  std::vector<adept_material> mats;
+  double range_cut = 0.7;
+  // geometry (host copy)
+  int kind = 0, n_vol = 0, n_bins = 0;
+  std::vector<double> bnd;
+  std::vector<int> vol_mat, vol_bin;
+  // arena
+  char* arena = nullptr;
+  size_t arena_bytes = 0, arena_used = 0;
+  Params P{};
+  MatDev* mat_dev = nullptr;
+  double* mat_in = nullptr;
+  BuildScratch scratch{};
+  double2 *g64 = nullptr, *e64 = nullptr, *p64 = nullptr;
+  float2 *g32 = nullptr, *e32 = nullptr, *p32 = nullptr;
+  double *re64 = nullptr, *rp64 = nullptr, *Tc = nullptr, *kc = nullptr;
+  float *re32 = nullptr, *rp32 = nullptr;
+  TrackIn* stage = nullptr;
+  uint32_t* stage_meta = nullptr;
+  uint32_t* stage_keys = nullptr;
+  size_t stage_cap = 0;
+  char* probe = nullptr;
+  size_t probe_bytes = 0;
+  bool built = false;
+  // host pinned buffers
+  Ctrl* h_ctrl = nullptr;
+  uint32_t* h_done = nullptr;
+  char* h_stage = nullptr;
+  size_t h_stage_bytes = 0;
+  // launch shape
+  int grid = 0, block = 256;
+  cudaGraphExec_t graph = nullptr;
+  int graph_gens = 0;
+  // requests
+  std::mutex mu;
+  std::condition_variable cv;
+  uint32_t next_id = 1;
+  std::deque<uint32_t> pending;
+  std::unordered_map<uint32_t, std::unique_ptr<Request>> reqs;
+  std::vector<uint32_t> slot_req;  // slot -> request id
+  SlotAlloc slots;
+  double energy_in_flight = 0.0;
+  size_t in_flight = 0;
+  adept_stats stats{};
+  std::vector<uint32_t> gen_log_host;
+};
+
+static int fail(adept_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(c, ADEPT_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static void* carve(adept_ctx* c, size_t bytes) {
+  const size_t off = (c->arena_used + 255) & ~(size_t)255;
+  if (off + bytes > c->arena_bytes) return nullptr;
+  c->arena_used = off + bytes;
+  return c->arena + off;
+}
+
+template <class T>
+static bool carve_n(adept_ctx* c, T** out, size_t n) {
+  *out = static_cast<T*>(carve(c, sizeof(T) * (n ? n : 1)));
+  return *out != nullptr;
+}
+
+// volumes of the calorimeter: slab planes, or tube radii with vacuum inside and between
+static int build_geometry(adept_ctx* c, const adept_geometry* g) {
+  if (g->kind != 0 && g->kind != 1) return fail(c, ADEPT_EINVAL, "geometry kind must be 0 or 1");
+  if (g->n_layers < 1 || g->n_mat_per_layer < 1 || g->n_mat_per_layer > 16 || !g->layer_materials || !g->thickness_mm)
+    return fail(c, ADEPT_EINVAL, "geometry needs n_layers >= 1 and 1..16 sublayers");
+  double lt = 0.0;
+  for (int s = 0; s < g->n_mat_per_layer; ++s) {
+    if (g->layer_materials[s] < 0 || g->layer_materials[s] >= c->n_mat)
+      return fail(c, ADEPT_EINVAL, "sublayer %d names material %d of %d", s, g->layer_materials[s], c->n_mat);
+    if (!(g->thickness_mm[s] > 0.0)) return fail(c, ADEPT_EINVAL, "sublayer %d thickness must be > 0", s);
+    lt += g->thickness_mm[s];
+  }
+  c->kind = g->kind;
+  c->n_bins = g->n_layers * g->n_mat_per_layer;
+  c->bnd.clear(); c->vol_mat.clear(); c->vol_bin.clear();
+  auto mat_of = [&](int s) { return c->mats[g->layer_materials[s]].Z > 0 ? g->layer_materials[s] : -1; };
+  if (g->kind == 0) {
+    if (!(g->transverse_half_mm > 0.0)) return fail(c, ADEPT_EINVAL, "transverse_half_mm must be > 0");
+    double z = 0.0;
+    c->bnd.push_back(0.0);
+    for (int l = 0; l < g->n_layers; ++l)
+      for (int s = 0; s < g->n_mat_per_layer; ++s) {
+        z += g->thickness_mm[s];
+        c->bnd.push_back(z);
+        const int m = mat_of(s);
+        c->vol_mat.push_back(m);
+        c->vol_bin.push_back(m >= 0 ? l * g->n_mat_per_layer + s : -1);
+      }
+  } else {
+    if (!g->layer_inner_r_mm || !(g->half_length_mm > 0.0)) return fail(c, ADEPT_EINVAL, "tubes need radii and half length");
+    for (int l = 0; l < g->n_layers; ++l) {
+      if (!(g->layer_inner_r_mm[l] > 0.0)) return fail(c, ADEPT_EINVAL, "layer radius must be > 0");
+      if (l + 1 < g->n_layers && !(g->layer_inner_r_mm[l] + lt <= g->layer_inner_r_mm[l + 1]))
+        return fail(c, ADEPT_EINVAL, "layer %d overlaps the next one", l);
+    }
+    c->bnd.push_back(g->layer_inner_r_mm[0]);  // volume 0: vacuum inside the first layer
+    c->vol_mat.push_back(-1);
+    c->vol_bin.push_back(-1);
+    for (int l = 0; l < g->n_layers; ++l) {
+      double r = g->layer_inner_r_mm[l];
+      for (int s = 0; s < g->n_mat_per_layer; ++s) {
+        r += g->thickness_mm[s];
+        c->bnd.push_back(r);
+        const int m = mat_of(s);
+        c->vol_mat.push_back(m);
+        c->vol_bin.push_back(m >= 0 ? l * g->n_mat_per_layer + s : -1);
+      }
+      if (l + 1 < g->n_layers) {  // vacuum gap up to the next layer
+        c->bnd.push_back(g->layer_inner_r_mm[l + 1]);
+        c->vol_mat.push_back(-1);
+        c->vol_bin.push_back(-1);
+      }
+    }
+  }
+  c->n_vol = (int)c->vol_mat.size();
+  if (c->n_vol > kMaxVol || c->n_vol > 65535) return fail(c, ADEPT_EINVAL, "too many volumes (%d)", c->n_vol);
+  return ADEPT_OK;
+}
+
+static size_t track_bytes(int precision) {
+  return 3 * 8 + 3 * (precision ? 4 : 8) + 8 + 8 + 3 * 4;
+}
+
+static bool carve_queue(adept_ctx* c, TrackSoA* q, uint32_t cap) {
+  const size_t du = c->opt.precision ? 4 : 8;
+  bool ok = carve_n(c, &q->x, cap) && carve_n(c, &q->y, cap) && carve_n(c, &q->z, cap);
+  q->ux = carve(c, du * cap); q->uy = carve(c, du * cap); q->uz = carve(c, du * cap);
+  ok = ok && q->ux && q->uy && q->uz;
+  ok = ok && carve_n(c, &q->E, cap) && carve_n(c, &q->id, cap) && carve_n(c, &q->ev, cap) &&
+       carve_n(c, &q->step, cap) && carve_n(c, &q->nav, cap);
+  return ok;
+}
+
+extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const adept_material* materials,
+                          int32_t n_materials, const adept_cuts* cuts, const adept_options* options, void* dev_arena,
+                          size_t arena_bytes, void* stream) {
+  if (!out || !geometry || !materials || !cuts || !dev_arena) return ADEPT_EINVAL;
+  *out = nullptr;
+  auto c = std::make_unique<adept_ctx>();
+  if (n_materials < 1 || n_materials > kMaxMat) return ADEPT_EINVAL;
+  if (reinterpret_cast<uintptr_t>(dev_arena) & 255) return ADEPT_EINVAL;
+  c->n_mat = n_materials;
+  c->mats.assign(materials, materials + n_materials);
+  for (auto& m : c->mats)
+    if (m.Z < 0 || m.Z > 100 || (m.Z > 0 && !(m.A_g_mol > 0 && m.density_g_cm3 > 0 && m.I_eV > 0))) return ADEPT_EINVAL;
+  if (!(cuts->range_cut_mm > 0.0) || !(cuts->tracking_cut_MeV >= 1e-3) || !(cuts->tracking_cut_MeV < 1e4))
+    return ADEPT_EINVAL;
+  if (options) c->opt = *options;
+  adept_options& o = c->opt;
+  if (o.precision != 0 && o.precision != 1) return ADEPT_EINVAL;
+  if (o.reserved != 0) return ADEPT_EINVAL;
+  if (o.block_size == 0) o.block_size = 256;
+  if (o.block_size < 32 || o.block_size > 256 || (o.block_size & 31)) return ADEPT_EINVAL;
+  if (o.graph_generations < 0 || o.graph_generations > 1024) return ADEPT_EINVAL;
+  if (o.seed == 0) o.seed = 1;
+  if (o.max_steps == 0) o.max_steps = 100000;
+  if (o.max_vacuum_steps == 0) o.max_vacuum_steps = 1000;
+  if (o.max_vacuum_steps > 65535) return ADEPT_EINVAL;
+  if (o.max_events == 0) o.max_events = 65536;
+  if (o.max_generation_log == 0) o.max_generation_log = 4096;
+  if (o.max_generation_log > (uint32_t)kMaxLogGen) o.max_generation_log = kMaxLogGen;
+  if (!(o.tracks_per_MeV > 0.0)) o.tracks_per_MeV = 0.25;
+  c->range_cut = cuts->range_cut_mm;
+  int rc = build_geometry(c.get(), geometry);
+  if (rc) return rc;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->arena = static_cast<char*>(dev_arena);
+  c->arena_bytes = arena_bytes;
+  adept_ctx* cp = c.get();
+  Params& P = c->P;
+  bool ok = carve_n(cp, &P.ctrl, 1);
+  double* bnd = nullptr; int *vm = nullptr, *vb = nullptr;
+  ok = ok && carve_n(cp, &bnd, c->bnd.size()) && carve_n(cp, &vm, c->n_vol) && carve_n(cp, &vb, c->n_vol);
+  ok = ok && carve_n(cp, &c->mat_dev, kMaxMat) && carve_n(cp, &c->mat_in, 4 * kMaxMat);
+  const size_t nn = (size_t)kNNode * n_materials;
+  ok = ok && carve_n(cp, &c->scratch.vals, 14 * nn) && carve_n(cp, &c->scratch.bins, 3 * nn);
+  ok = ok && carve_n(cp, &c->g64, nn * kNTabG) && carve_n(cp, &c->e64, nn * kNTabE) && carve_n(cp, &c->p64, nn * kNTabP);
+  ok = ok && carve_n(cp, &c->g32, nn * kNTabG) && carve_n(cp, &c->e32, nn * kNTabE) && carve_n(cp, &c->p32, nn * kNTabP);
+  ok = ok && carve_n(cp, &c->re64, nn) && carve_n(cp, &c->rp64, nn) && carve_n(cp, &c->re32, nn) && carve_n(cp, &c->rp32, nn);
+  ok = ok && carve_n(cp, &c->Tc, kMaxMat) && carve_n(cp, &c->kc, kMaxMat);
+  EventView& E = P.evt;
+  const uint32_t ms = o.max_events;
+  ok = ok && carve_n(cp, &E.key, ms) && carve_n(cp, &E.state, ms) && carve_n(cp, &E.alive, ms) &&
+       carve_n(cp, &E.edep, (size_t)ms * c->n_bins) && carve_n(cp, &E.leaked, ms) && carve_n(cp, &E.killed, ms) &&
+       carve_n(cp, &E.done_list, ms);
+  ok = ok && carve_n(cp, &P.gen_log, 3 * (size_t)o.max_generation_log);
+  c->probe_bytes = (size_t)8 << 20;
+  c->probe = static_cast<char*>(carve(cp, c->probe_bytes));
+  ok = ok && c->probe;
+  if (!ok) return ADEPT_ENOMEM;
+  // the remainder: primary staging (1/16, at least room for 4096 tracks) and the queues
+  const size_t per_track = track_bytes(o.precision);
+  size_t rest = c->arena_bytes - ((c->arena_used + 255) & ~(size_t)255);
+  size_t stage_cap = std::max<size_t>(4096, rest / 16 / (sizeof(TrackIn) + 12));
+  stage_cap = std::min<size_t>(stage_cap, (size_t)1 << 22);
+  ok = carve_n(cp, &c->stage, stage_cap) && carve_n(cp, &c->stage_meta, 2 * stage_cap) &&
+       carve_n(cp, &c->stage_keys, stage_cap);
+  if (!ok) return ADEPT_ENOMEM;
+  c->stage_cap = stage_cap;
+  rest = c->arena_bytes - ((c->arena_used + 255) & ~(size_t)255);
+  uint64_t cap = rest / (6 * per_track + 6 * 256);
+  if (o.track_capacity) {
+    if (o.track_capacity > cap) return ADEPT_ENOMEM;
+    cap = o.track_capacity;
+  }
+  cap = std::min<uint64_t>(cap, 0xFFFFFFF0ull);
+  if (cap < 1024) return ADEPT_ENOMEM;
+  o.track_capacity = cap;
+  for (int par = 0; par < 2; ++par)
+    for (int s = 0; s < 3; ++s)
+      if (!carve_queue(cp, &P.q[par][s], (uint32_t)cap)) return ADEPT_ENOMEM;
+  P.cap = (uint32_t)cap;
+  // views
+  P.geo.kind = c->kind; P.geo.n_vol = c->n_vol; P.geo.n_bins = c->n_bins;
+  P.geo.half_xy = geometry->transverse_half_mm; P.geo.half_z = geometry->half_length_mm;
+  P.geo.bnd = bnd; P.geo.vol_mat = vm; P.geo.vol_bin = vb;
+  P.mat = c->mat_dev;
+  P.tab = TableView{c->g64, c->e64, c->p64, c->g32, c->e32, c->p32, c->re64, c->rp64, c->re32, c->rp32, c->Tc, c->kc};
+  E.max_slots = ms;
+  P.max_log = o.max_generation_log;
+  P.field_T = cuts->field_T;
+  P.tcut = cuts->tracking_cut_MeV;
+  P.seed = o.seed; P.process_mask = o.process_mask; P.max_steps = o.max_steps; P.max_vac = o.max_vacuum_steps;
+  // device state
+  adept_ctx* c_ = cp;
+  {
+    adept_ctx* c = c_;
+    CK(cudaMemcpyAsync(bnd, c->bnd.data(), sizeof(double) * c->bnd.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(vm, c->vol_mat.data(), sizeof(int) * c->n_vol, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(vb, c->vol_bin.data(), sizeof(int) * c->n_vol, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), c->stream));
+    CK(cudaMemsetAsync(E.state, 0, sizeof(uint32_t) * ms, c->stream));
+    CK(cudaHostAlloc(&c->h_ctrl, sizeof(Ctrl), cudaHostAllocDefault));
+    CK(cudaHostAlloc(&c->h_done, sizeof(uint32_t) * kDoneChunk, cudaHostAllocDefault));
+    CK(cudaStreamSynchronize(c->stream));
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int bps = step_kernel_max_blocks_per_sm(o.precision, o.block_size);
+    if (bps < 1) bps = 1;
+    if (o.blocks_per_sm > 0) bps = std::min(bps, (int)o.blocks_per_sm);
+    c->block = o.block_size;
+    c->grid = sms * bps;
+  }
+  c->slots.init(ms);
+  c->slot_req.assign(ms, 0);
+  *out = c.release();
+  return ADEPT_OK;
+}
+
+extern "C" int adept_build_tables(adept_ctx* c) {
+  if (!c) return ADEPT_EINVAL;
+  std::vector<double> in(4 * kMaxMat, 0.0);
+  for (int m = 0; m < c->n_mat; ++m) {
+    in[4 * m] = c->mats[m].Z; in[4 * m + 1] = c->mats[m].A_g_mol;
+    in[4 * m + 2] = c->mats[m].density_g_cm3; in[4 * m + 3] = c->mats[m].I_eV;
+  }
+  CK(cudaMemcpyAsync(c->mat_in, in.data(), sizeof(double) * in.size(), cudaMemcpyHostToDevice, c->stream));
+  CK(launch_build_tables(c->P, c->mat_in, c->n_mat, c->range_cut, c->mat_dev, c->scratch, c->g64, c->e64, c->p64,
+                         c->g32, c->e32, c->p32, c->re64, c->rp64, c->re32, c->rp32, c->Tc, c->kc, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->stats.launches += 6;
+  c->built = true;
+  return ADEPT_OK;
+}
+
+// event numbering of a request: events in first-appearance order, tracks numbered 1, 2, ...
+// within their event
+template <class FE, class FP, class FX>
+static int prepare_request(adept_ctx* c, Request& r, FE ev_at, FP pdg_at, FX e_at) {
+  std::unordered_map<uint32_t, uint32_t> idx;
+  std::vector<uint32_t> count;
+  r.meta.resize(2 * r.n);
+  r.energy = 0.0;
+  for (size_t i = 0; i < r.n; ++i) {
+    const uint32_t ev = ev_at(i);
+    auto it = idx.find(ev);
+    uint32_t k;
+    if (it == idx.end()) {
+      k = (uint32_t)r.keys.size();
+      idx.emplace(ev, k);
+      r.keys.push_back(ev);
+      count.push_back(0);
+    } else {
+      k = it->second;
+    }
+    r.meta[2 * i] = k;
+    r.meta[2 * i + 1] = ++count[k];
+    const int32_t p = pdg_at(i);
+    const double e = e_at(i);
+    if (p != 22 && p != 11 && p != -11) return fail(c, ADEPT_EINVAL, "track %zu: pdg %d is not e-, e+ or gamma", i, p);
+    if (!(e >= 0.0 && e <= 1e6)) return fail(c, ADEPT_EINVAL, "track %zu: energy %g outside [0, 1e6] MeV", i, e);
+    r.energy += e + (p == -11 ? 2 * 0.51099895 : 0.0);
+  }
+  if (r.keys.size() > c->opt.max_events) return fail(c, ADEPT_EINVAL, "request has more events than event slots");
+  if (r.n > c->stage_cap)
+    return fail(c, ADEPT_EINVAL, "request of %zu tracks exceeds the staging capacity %zu", r.n, c->stage_cap);
+  return ADEPT_OK;
+}
+
+static int enqueue(adept_ctx* c, std::unique_ptr<Request> r, uint32_t* request_id) {
+  std::lock_guard<std::mutex> lk(c->mu);
+  r->id = c->next_id++;
+  if (c->next_id == 0) c->next_id = 1;
+  r->t_submit = Clock::now();
+  *request_id = r->id;
+  if (r->n == 0) {
+    r->state = 2;
+    r->t_done = r->t_submit;
+    c->reqs.emplace(r->id, std::move(r));
+    c->cv.notify_all();
+    return ADEPT_OK;
+  }
+  c->pending.push_back(r->id);
+  c->reqs.emplace(r->id, std::move(r));
+  return ADEPT_OK;
+}
+
+extern "C" int adept_submit(adept_ctx* c, const adept_track* host_tracks, size_t n, uint32_t* request_id) {
+  if (!c || !request_id || (n && !host_tracks)) return ADEPT_EINVAL;
+  auto r = std::make_unique<Request>();
+  r->n = n;
+  r->host.assign(host_tracks, host_tracks + n);
+  const adept_track* h = r->host.data();
+  for (size_t i = 0; i < n; ++i) {
+    const double* d = h[i].dir;
+    const double nn = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(fabs(nn - 1.0) < 1e-6)) return fail(c, ADEPT_EINVAL, "track %zu: direction is not a unit vector", i);
+  }
+  int rc = prepare_request(
+      c, *r, [&](size_t i) { return h[i].event; }, [&](size_t i) { return h[i].pdg; },
+      [&](size_t i) { return h[i].E_kin_MeV; });
+  if (rc) return rc;
+  return enqueue(c, std::move(r), request_id);
+}
+
+extern "C" int adept_submit_device(adept_ctx* c, const void* dev_tracks, size_t n, uint32_t* request_id) {
+  if (!c || !request_id || (n && !dev_tracks)) return ADEPT_EINVAL;
+  auto r = std::make_unique<Request>();
+  r->n = n;
+  r->dev = static_cast<const adept_track*>(dev_tracks);
+  std::vector<uint32_t> ev(n);
+  std::vector<int32_t> pdg(n);
+  std::vector<double> E(n);
+  if (n) {
+    // read back the three fields the host needs for numbering and admission
+    const char* base = static_cast<const char*>(dev_tracks);
+    CK(cudaMemcpy2DAsync(ev.data(), 4, base + offsetof(adept_track, event), sizeof(adept_track), 4, n,
+                         cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpy2DAsync(pdg.data(), 4, base + offsetof(adept_track, pdg), sizeof(adept_track), 4, n,
+                         cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpy2DAsync(E.data(), 8, base + offsetof(adept_track, E_kin_MeV), sizeof(adept_track), 8, n,
+                         cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  int rc = prepare_request(
+      c, *r, [&](size_t i) { return ev[i]; }, [&](size_t i) { return pdg[i]; }, [&](size_t i) { return E[i]; });
+  if (rc) return rc;
+  return enqueue(c, std::move(r), request_id);
+}
+
+// ---------------------------------------------------------------- admission
+static int ensure_host_stage(adept_ctx* c, size_t bytes) {
+  if (c->h_stage_bytes >= bytes) return ADEPT_OK;
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  c->h_stage = nullptr;
+  c->h_stage_bytes = 0;
+  const size_t want = std::max(bytes, (size_t)1 << 20);
+  CK(cudaHostAlloc(&c->h_stage, want, cudaHostAllocDefault));
+  c->h_stage_bytes = want;
+  return ADEPT_OK;
+}
+
+// Admit pending requests in arrival order while event slots, staging room and the
+// track budget allow (an idle device always admits the next request).
+static int admit(adept_ctx* c) {
+  size_t used = 0;
+  const double budget = (double)c->P.cap / c->opt.tracks_per_MeV;
+  for (;;) {
+    Request* r;
+    {
+      std::lock_guard<std::mutex> lk(c->mu);
+      if (c->pending.empty()) return ADEPT_OK;
+      r = c->reqs.at(c->pending.front()).get();
+      if (used + r->n > c->stage_cap) return ADEPT_OK;
+      if (c->in_flight > 0 && c->energy_in_flight + r->energy > budget) return ADEPT_OK;
+      uint32_t base;
+      if (!c->slots.alloc((uint32_t)r->keys.size(), &base)) return ADEPT_OK;
+      r->slot_base = base;
+      c->pending.pop_front();
+      r->state = 1;
+      r->remaining = (uint32_t)r->keys.size();
+      for (uint32_t k = 0; k < r->remaining; ++k) c->slot_req[base + k] = r->id;
+      c->energy_in_flight += r->energy;
+      c->in_flight++;
+    }
+    const size_t nk = r->keys.size();
+    // pinned staging: tracks (host submissions), meta, keys
+    const size_t tb = r->dev ? 0 : sizeof(adept_track) * r->n;
+    const size_t mb = sizeof(uint32_t) * 2 * r->n, kb = sizeof(uint32_t) * nk;
+    int rc = ensure_host_stage(c, tb + mb + kb + 64);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));  // the pinned buffer may still feed an earlier copy
+    char* h = c->h_stage;
+    if (tb) memcpy(h, r->host.data(), tb);
+    memcpy(h + tb, r->meta.data(), mb);
+    memcpy(h + tb + mb, r->keys.data(), kb);
+    TrackIn* dst = c->stage + used;
+    const TrackIn* src = r->dev ? reinterpret_cast<const TrackIn*>(r->dev) : dst;
+    if (tb) CK(cudaMemcpyAsync(dst, h, tb, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->stage_meta + 2 * used, h + tb, mb, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->stage_keys, h + tb + mb, kb, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_admit(c->P, r->slot_base, c->stage_keys, (int)nk, c->stream));
+    CK(launch_init_primaries(c->P, src, c->stage_meta + 2 * used, (int)r->n, r->slot_base, c->opt.precision, c->stream));
+    c->stats.launches += 2;
+    used += r->n;
+  }
+}
+
+// ---------------------------------------------------------------- generation chunks
+static int capture_graph(adept_ctx* c, int gens) {
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemsetAsync(&c->P.ctrl->done_count, 0, sizeof(uint32_t), c->stream);
+  for (int k = 0; k < gens && e == cudaSuccess; ++k) e = launch_step(c->P, c->opt.precision, c->grid, c->block, c->stream);
+  if (e == cudaSuccess) e = launch_finish(c->P, c->opt.precision, c->stream);
+  cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+  if (e != cudaSuccess) return fail(c, ADEPT_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return fail(c, ADEPT_ECUDA, "graph capture end: %s", cudaGetErrorString(e2));
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, ADEPT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  c->graph_gens = gens;
+  return ADEPT_OK;
+}
+
+// Run one chunk of generations, then read the control block and the done list.
+static int run_chunk(adept_ctx* c) {
+  const int G = c->opt.graph_generations;
+  if (G > 0) {
+    if (!c->graph) {
+      int rc = capture_graph(c, G);
+      if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(c->graph, c->stream));
+    c->stats.launches += G + 2;
+  } else {
+    CK(cudaMemsetAsync(&c->P.ctrl->done_count, 0, sizeof(uint32_t), c->stream));
+    CK(launch_step(c->P, c->opt.precision, c->grid, c->block, c->stream));
+    CK(launch_finish(c->P, c->opt.precision, c->stream));
+    c->stats.launches += 3;
+  }
+  CK(cudaMemcpyAsync(c->h_ctrl, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_done, c->P.evt.done_list, sizeof(uint32_t) * kDoneChunk, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ADEPT_OK;
+}
+
+// copy a finished request's rows back and release its slots
+static int complete(adept_ctx* c, Request* r) {
+  const size_t nk = r->keys.size(), nb = c->n_bins;
+  r->edep.resize(nk * nb);
+  r->leaked.resize(nk);
+  r->killed.resize(nk);
+  if (nk) {
+    CK(cudaMemcpyAsync(r->edep.data(), c->P.evt.edep + (size_t)r->slot_base * nb, sizeof(double) * nk * nb,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(r->leaked.data(), c->P.evt.leaked + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync(r->killed.data(), c->P.evt.killed + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemsetAsync(c->P.evt.state + r->slot_base, 0, sizeof(uint32_t) * nk, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->slots.release(r->slot_base, (uint32_t)nk);
+  c->energy_in_flight -= r->energy;
+  if (c->energy_in_flight < 0) c->energy_in_flight = 0;
+  c->in_flight--;
+  r->state = 2;
+  r->t_done = Clock::now();
+  r->dev = nullptr;
+  std::vector<adept_track>().swap(r->host);
+  std::vector<uint32_t>().swap(r->meta);
+  c->stats.requests_done++;
+  c->cv.notify_all();
+  return ADEPT_OK;
+}
+
+extern "C" int adept_transport(adept_ctx* c, uint64_t timeout_us) {
+  if (!c) return ADEPT_EINVAL;
+  if (!c->built) return fail(c, ADEPT_ESTATE, "adept_build_tables has not run");
+  const auto t0 = Clock::now();
+  std::vector<uint32_t> done;
+  int idle_chunks = 0;
+  for (;;) {
+    int rc = admit(c);
+    if (rc) return rc;
+    {
+      std::lock_guard<std::mutex> lk(c->mu);
+      if (c->in_flight == 0 && c->pending.empty()) return ADEPT_OK;
+    }
+    rc = run_chunk(c);
+    if (rc) return rc;
+    const Ctrl& h = *c->h_ctrl;
+    for (int k = 0; k < 3; ++k) { c->stats.steps[k] = h.steps[k]; c->stats.secondaries[k] = h.created[k]; }
+    c->stats.generations = h.generations;
+    c->stats.overflow = h.overflow;
+    const uint32_t nd = h.done_count;
+    done.assign(c->h_done, c->h_done + std::min(nd, kDoneChunk));
+    if (nd > kDoneChunk) {
+      done.resize(nd);
+      CK(cudaMemcpy(done.data() + kDoneChunk, c->P.evt.done_list + kDoneChunk, sizeof(uint32_t) * (nd - kDoneChunk),
+                    cudaMemcpyDeviceToHost));
+    }
+    for (uint32_t s : done) {
+      Request* r;
+      {
+        std::lock_guard<std::mutex> lk(c->mu);
+        auto it = c->reqs.find(c->slot_req[s]);
+        if (it == c->reqs.end()) continue;
+        r = it->second.get();
+      }
+      if (r->state == 1 && r->remaining > 0 && --r->remaining == 0) {
+        rc = complete(c, r);
+        if (rc) return rc;
+      }
+    }
+    const uint32_t live = h.count[h.gen & 1][0] + h.count[h.gen & 1][1] + h.count[h.gen & 1][2];
+    idle_chunks = (live == 0 && done.empty()) ? idle_chunks + 1 : 0;
+    if (idle_chunks > 4) {
+      std::lock_guard<std::mutex> lk(c->mu);
+      if (c->in_flight > 0) return fail(c, ADEPT_ESTATE, "requests in flight but no live tracks (internal error)");
+    }
+    if (h.overflow) return fail(c, ADEPT_ENOMEM, "%llu tracks exceeded the queue capacity %u; results are incomplete",
+                                (unsigned long long)h.overflow, c->P.cap);
+    if (timeout_us) {
+      const auto us = std::chrono::duration_cast<std::chrono::microseconds>(Clock::now() - t0).count();
+      if ((uint64_t)us >= timeout_us) return fail(c, ADEPT_ETIMEOUT, "transport stopped after %llu us", (unsigned long long)us);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- results
+extern "C" int adept_poll(adept_ctx* c, uint32_t id) {
+  if (!c) return ADEPT_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->reqs.find(id);
+  if (it == c->reqs.end()) return ADEPT_ENOTFOUND;
+  return it->second->state == 2 ? 1 : 0;
+}
+
+extern "C" int adept_wait(adept_ctx* c, uint32_t id, uint64_t timeout_us) {
+  if (!c) return ADEPT_EINVAL;
+  std::unique_lock<std::mutex> lk(c->mu);
+  auto pred = [&] {
+    auto it = c->reqs.find(id);
+    return it == c->reqs.end() || it->second->state == 2;
+  };
+  if (timeout_us == 0) c->cv.wait(lk, pred);
+  else if (!c->cv.wait_for(lk, std::chrono::microseconds(timeout_us), pred)) return ADEPT_ETIMEOUT;
+  return c->reqs.count(id) ? ADEPT_OK : ADEPT_ENOTFOUND;
+}
+
+extern "C" int adept_get_scoring(adept_ctx* c, uint32_t id, double* edep_out, size_t n, adept_result* meta) {
+  if (!c) return ADEPT_EINVAL;
+  std::unique_ptr<Request> r;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->reqs.find(id);
+    if (it == c->reqs.end()) return ADEPT_ENOTFOUND;
+    if (it->second->state != 2) return ADEPT_EBUSY;
+    const size_t need = it->second->keys.size() * (size_t)c->n_bins;
+    if (need && (!edep_out || n < need)) return fail(c, ADEPT_EINVAL, "edep_out holds %zu doubles, %zu needed", n, need);
+    r = std::move(it->second);
+    c->reqs.erase(it);
+  }
+  if (!r->edep.empty()) memcpy(edep_out, r->edep.data(), sizeof(double) * r->edep.size());
+  if (meta) {
+    meta->request = r->id;
+    meta->n_events = (uint32_t)r->keys.size();
+    meta->n_bins = (uint32_t)c->n_bins;
+    double d = 0, l = 0, k = 0;
+    for (double v : r->edep) d += v;
+    for (double v : r->leaked) l += v;
+    for (double v : r->killed) k += v;
+    meta->deposited_MeV = d;
+    meta->leaked_MeV = l;
+    meta->killed_MeV = k;
+    meta->latency_us = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
+  }
+  return ADEPT_OK;
+}
+
+extern "C" int adept_get_stats(adept_ctx* c, adept_stats* out) {
+  if (!c || !out) return ADEPT_EINVAL;
+  *out = c->stats;
+  return ADEPT_OK;
+}
+
+extern "C" int adept_get_generation_log(adept_ctx* c, uint32_t* host_out, size_t n_max) {
+  if (!c || (n_max && !host_out)) return ADEPT_EINVAL;
+  Ctrl h;
+  CK(cudaMemcpyAsync(&h, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const size_t n = std::min<size_t>(h.log_n, n_max);
+  if (n) {
+    CK(cudaMemcpyAsync(host_out, c->P.gen_log, sizeof(uint32_t) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return (int)n;
+}
+
+extern "C" int adept_reset_generation_log(adept_ctx* c) {
+  if (!c) return ADEPT_EINVAL;
+  CK(cudaMemsetAsync(&c->P.ctrl->log_n, 0, sizeof(uint32_t), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ADEPT_OK;
+}
+
+extern "C" int adept_get_cuts(adept_ctx* c, int32_t m, double* e_cut, double* gamma_cut) {
+  if (!c || !e_cut || !gamma_cut || m < 0 || m >= c->n_mat) return ADEPT_EINVAL;
+  if (!c->built) return fail(c, ADEPT_ESTATE, "tables not built");
+  CK(cudaMemcpy(e_cut, c->Tc + m, sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(gamma_cut, c->kc + m, sizeof(double), cudaMemcpyDeviceToHost));
+  return ADEPT_OK;
+}
+
+static int ntab(int s) { return s == 0 ? kNTabG : (s == 1 ? kNTabE : kNTabP); }
+
+extern "C" int adept_get_table(adept_ctx* c, int32_t s, int32_t t, int32_t m, int32_t prec, double* host_out) {
+  if (!c || !host_out || s < 0 || s > 2 || t < 0 || t >= ntab(s) || m < 0 || m >= c->n_mat || (prec != 0 && prec != 1))
+    return ADEPT_EINVAL;
+  if (!c->built) return fail(c, ADEPT_ESTATE, "tables not built");
+  const int nt = ntab(s);
+  const size_t off = ((size_t)m * kNNode) * nt;
+  if (prec == 0) {
+    std::vector<double2> rec((size_t)kNNode * nt);
+    const double2* src = (s == 0 ? c->g64 : (s == 1 ? c->e64 : c->p64)) + off;
+    CK(cudaMemcpy(rec.data(), src, sizeof(double2) * rec.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < kNNode; ++i) host_out[i] = rec[(size_t)i * nt + t].x;
+  } else {
+    std::vector<float2> rec((size_t)kNNode * nt);
+    const float2* src = (s == 0 ? c->g32 : (s == 1 ? c->e32 : c->p32)) + off;
+    CK(cudaMemcpy(rec.data(), src, sizeof(float2) * rec.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < kNNode; ++i) host_out[i] = rec[(size_t)i * nt + t].x;
+  }
+  return ADEPT_OK;
+}
+
+// ---------------------------------------------------------------- probes
+template <class F>
+static int probe_run(adept_ctx* c, size_t in_bytes_per, size_t out_bytes_per, size_t n, F fn) {
+  const size_t per = in_bytes_per + out_bytes_per + 64;
+  const size_t chunk = std::max<size_t>(1, c->probe_bytes / per / 2);
+  for (size_t b = 0; b < n; b += chunk) {
+    const size_t k = std::min(chunk, n - b);
+    int rc = fn(b, k);
+    if (rc) return rc;
+  }
+  return ADEPT_OK;
+}
+
+extern "C" int adept_probe_philox(adept_ctx* c, const uint32_t key[2], const uint32_t* host_ctr, size_t n,
+                                  uint32_t* host_out) {
+  if (!c || !key || (n && (!host_ctr || !host_out))) return ADEPT_EINVAL;
+  return probe_run(c, 16, 16, n, [&](size_t b, size_t k) {
+    uint32_t* din = reinterpret_cast<uint32_t*>(c->probe);
+    uint32_t* dout = din + 4 * k;
+    CK(cudaMemcpyAsync(din, host_ctr + 4 * b, 16 * k, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_probe_philox(din, (int)k, key[0], key[1], dout, c->stream));
+    CK(cudaMemcpyAsync(host_out + 4 * b, dout, 16 * k, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ADEPT_OK;
+  });
+}
+
+extern "C" int adept_probe_interp(adept_ctx* c, int32_t s, int32_t t, int32_t m, int32_t prec, const double* host_E,
+                                  size_t n, double* host_out) {
+  if (!c || s < 0 || s > 2 || t < 0 || t >= ntab(s) || m < 0 || m >= c->n_mat || (prec != 0 && prec != 1) ||
+      (n && (!host_E || !host_out)))
+    return ADEPT_EINVAL;
+  if (!c->built) return fail(c, ADEPT_ESTATE, "tables not built");
+  return probe_run(c, 8, 8, n, [&](size_t b, size_t k) {
+    double* din = reinterpret_cast<double*>(c->probe);
+    double* dout = din + k;
+    CK(cudaMemcpyAsync(din, host_E + b, 8 * k, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_probe_interp(c->P, s, t, m, prec, din, (int)k, dout, c->stream));
+    CK(cudaMemcpyAsync(host_out + b, dout, 8 * k, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ADEPT_OK;
+  });
+}
+
+extern "C" int adept_probe_inverse_range(adept_ctx* c, int32_t s, int32_t m, int32_t prec, const double* host_R,
+                                         size_t n, double* host_out) {
+  if (!c || s < 1 || s > 2 || m < 0 || m >= c->n_mat || (prec != 0 && prec != 1) || (n && (!host_R || !host_out)))
+    return ADEPT_EINVAL;
+  if (!c->built) return fail(c, ADEPT_ESTATE, "tables not built");
+  return probe_run(c, 8, 8, n, [&](size_t b, size_t k) {
+    double* din = reinterpret_cast<double*>(c->probe);
+    double* dout = din + k;
+    CK(cudaMemcpyAsync(din, host_R + b, 8 * k, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_probe_inverse_range(c->P, s, m, prec, din, (int)k, dout, c->stream));
+    CK(cudaMemcpyAsync(host_out + b, dout, 8 * k, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ADEPT_OK;
+  });
+}
+
+extern "C" int adept_probe_distance(adept_ctx* c, int32_t prec, const double* host_pos, const double* host_dir,
+                                    const int32_t* host_vol, const double* host_T, const int32_t* host_charge, size_t n,
+                                    double* host_s, int32_t* host_next) {
+  if (!c || (prec != 0 && prec != 1)) return ADEPT_EINVAL;
+  if (n && (!host_pos || !host_dir || !host_vol || !host_T || !host_charge || !host_s || !host_next)) return ADEPT_EINVAL;
+  for (size_t i = 0; i < n; ++i)
+    if (host_vol[i] < 0 || host_vol[i] >= c->n_vol) return fail(c, ADEPT_EINVAL, "point %zu: volume out of range", i);
+  return probe_run(c, 64, 16, n, [&](size_t b, size_t k) {
+    char* p = c->probe;
+    double* dpos = reinterpret_cast<double*>(p);
+    double* ddir = dpos + 3 * k;
+    double* dT = ddir + 3 * k;
+    double* ds = dT + k;
+    int* dvol = reinterpret_cast<int*>(ds + k);
+    int* dq = dvol + k;
+    int* dnx = dq + k;
+    CK(cudaMemcpyAsync(dpos, host_pos + 3 * b, 24 * k, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(ddir, host_dir + 3 * b, 24 * k, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(dT, host_T + b, 8 * k, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(dvol, host_vol + b, 4 * k, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(dq, host_charge + b, 4 * k, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_probe_distance(c->P, prec, dpos, ddir, dvol, dT, dq, (int)k, ds, dnx, c->stream));
+    CK(cudaMemcpyAsync(host_s + b, ds, 8 * k, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(host_next + b, dnx, 4 * k, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ADEPT_OK;
+  });
+}
+
+extern "C" int adept_probe_sample(adept_ctx* c, int32_t which, int32_t m, int32_t prec, double E, uint32_t event,
+                                  size_t n, double* host_out) {
+  if (!c || which < 0 || which > 6 || m < 0 || m >= c->n_mat || (prec != 0 && prec != 1) || (n && !host_out))
+    return ADEPT_EINVAL;
+  if (!c->built) return fail(c, ADEPT_ESTATE, "tables not built");
+  if (n > c->probe_bytes / 96) return fail(c, ADEPT_EINVAL, "at most %zu draws per call", c->probe_bytes / 96);
+  double* dout = reinterpret_cast<double*>(c->probe);
+  CK(launch_probe_sample(c->P, which, m, prec, E, event, (int)n, dout, c->stream));
+  CK(cudaMemcpyAsync(host_out, dout, 96 * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ADEPT_OK;
+}
+
+extern "C" const char* adept_last_error(const adept_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" void adept_destroy(adept_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
+  if (c->h_done) cudaFreeHost(c->h_done);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  delete c;
+}

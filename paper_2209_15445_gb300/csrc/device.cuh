@@ -1,0 +1,697 @@
+// Device building blocks of the shower transport: Philox streams, table lookups, the
+// interaction samplers, slab/tube navigation and the analytic helix. Everything is a
+// template on the arithmetic type R of the physics: double for the plain FP64 form,
+// float for the split form (positions, boundary distances and energies stay double).
+#pragma once
+#include <cstdint>
+
+#include "layout.h"
+
+namespace adept {
+
+// ---------------------------------------------------------------- constants (PDG/CODATA)
+constexpr double kMe = 0.51099895;        // electron mass, MeV
+constexpr double kRe = 2.8179403262e-12;  // classical electron radius, mm
+constexpr double kAlpha = 1.0 / 137.035999084;
+constexpr double kNA = 6.02214076e23;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kHelixK = 0.299792458;   // rho[mm] = p[MeV] / (K B[T])
+constexpr double kAlphaR = 0.2;           // step function: max(alpha_R R, min(R, rho_f))
+constexpr double kRhoF = 1.0;             // mm
+constexpr double kBig = 1e300;
+// energy grid: ln(1 keV), ln(10)/32 and its inverse, as correctly rounded doubles
+constexpr double kLnEmin = -6.907755278982137;
+constexpr double kDlog = 0.07195578415606393;
+constexpr double kInvDlog = 13.897423420904056;
+
+// numeric helpers per precision
+template <class R> struct M;
+template <> struct M<double> {
+  static __device__ __forceinline__ double log(double x) { return ::log(x); }
+  static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }
+  static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+  static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  static __device__ __forceinline__ double acos(double x) { return ::acos(x); }
+  static __device__ __forceinline__ double atan2(double y, double x) { return ::atan2(y, x); }
+  static __device__ __forceinline__ double fmod(double x, double y) { return ::fmod(x, y); }
+  static __device__ __forceinline__ void sincos(double x, double* s, double* c) { ::sincos(x, s, c); }
+  static __device__ __forceinline__ double cos(double x) { return ::cos(x); }
+  static __device__ __forceinline__ double sin(double x) { return ::sin(x); }
+  static __device__ __forceinline__ double floor(double x) { return ::floor(x); }
+  static __host__ __device__ constexpr double big() { return 1e300; }
+  static __host__ __device__ constexpr double turn_tol() { return 0.0; }
+};
+template <> struct M<float> {
+  static __device__ __forceinline__ float log(float x) { return ::logf(x); }
+  static __device__ __forceinline__ float log1p(float x) { return ::log1pf(x); }
+  static __device__ __forceinline__ float exp(float x) { return ::expf(x); }
+  static __device__ __forceinline__ float sqrt(float x) { return ::sqrtf(x); }
+  static __device__ __forceinline__ float acos(float x) { return ::acosf(x); }
+  static __device__ __forceinline__ float atan2(float y, float x) { return ::atan2f(y, x); }
+  static __device__ __forceinline__ float fmod(float x, float y) { return ::fmodf(x, y); }
+  static __device__ __forceinline__ void sincos(float x, float* s, float* c) { ::sincosf(x, s, c); }
+  static __device__ __forceinline__ float cos(float x) { return ::cosf(x); }
+  static __device__ __forceinline__ float sin(float x) { return ::sinf(x); }
+  static __device__ __forceinline__ float floor(float x) { return ::floorf(x); }
+  static __host__ __device__ constexpr float big() { return 1e30f; }
+  // a helix root within this many radians below a full turn is the current point seen
+  // through FP32 rounding of the phase: treat it as an immediate crossing
+  static __host__ __device__ constexpr float turn_tol() { return 2e-5f; }
+};
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon et al., SC'11: ten rounds; each multiplies counter words 0 and 2 by fixed odd
+// constants, crosses the high halves with words 1 and 3 and the round key, and bumps
+// the key by the Weyl increments 0x9E3779B9 / 0xBB67AE85.
+struct U4 { uint32_t a, b, c, d; };
+
+__device__ __forceinline__ U4 philox(U4 x, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * x.a, hi0 = __umulhi(0xD2511F53u, x.a);
+    const uint32_t lo1 = 0xCD9E8D57u * x.c, hi1 = __umulhi(0xCD9E8D57u, x.c);
+    x = U4{hi1 ^ x.b ^ k0, lo1, hi0 ^ x.d ^ k1, lo0};
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return x;
+}
+
+// centred uniforms that can never round to 0 or 1
+__device__ __forceinline__ double u01d(uint32_t hi, uint32_t lo) {
+  const uint64_t x = ((uint64_t)hi << 20) ^ (uint64_t)(lo >> 12);  // 52 bits
+  return ((double)x + 0.5) * (1.0 / 4503599627370496.0);
+}
+__device__ __forceinline__ float u01f(uint32_t w) {
+  return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f);  // 23 bits
+}
+
+// Random stream of one (track, step): counter (id lo, id hi, step, block). Block 0 is
+// read separately for the interaction length and the process choice; model sampling
+// takes blocks 1, 2, ..., two uniforms per block from the word pairs (w0, w1) and
+// (w2, w3). The FP32 form takes the top 23 bits of the first word of each pair, so both
+// forms walk the same positions of the same stream and a split-precision history stays
+// paired with its FP64 counterpart until rounding changes a decision.
+template <class R> struct Stream;
+template <> struct Stream<double> {
+  uint32_t k0, k1, c0, c1, c2, blk;
+  U4 w;
+  int used;
+  __device__ Stream(uint32_t seed, uint32_t ev, uint64_t id, uint32_t step)
+      : k0(seed), k1(ev), c0((uint32_t)id), c1((uint32_t)(id >> 32)), c2(step), blk(0), used(4) {}
+  __device__ __forceinline__ void block0(double* u0, double* u1) const {
+    const U4 r = philox(U4{c0, c1, c2, 0u}, k0, k1);
+    *u0 = u01d(r.a, r.b);
+    *u1 = u01d(r.c, r.d);
+  }
+  __device__ __forceinline__ double next() {
+    if (used >= 4) { w = philox(U4{c0, c1, c2, ++blk}, k0, k1); used = 0; }
+    const double u = used == 0 ? u01d(w.a, w.b) : u01d(w.c, w.d);
+    used += 2;
+    return u;
+  }
+};
+template <> struct Stream<float> {
+  uint32_t k0, k1, c0, c1, c2, blk;
+  uint32_t w0, w2;
+  int used;
+  __device__ Stream(uint32_t seed, uint32_t ev, uint64_t id, uint32_t step)
+      : k0(seed), k1(ev), c0((uint32_t)id), c1((uint32_t)(id >> 32)), c2(step), blk(0), used(2) {}
+  __device__ __forceinline__ void block0(float* u0, float* u1) const {
+    const U4 r = philox(U4{c0, c1, c2, 0u}, k0, k1);
+    *u0 = u01f(r.a);
+    *u1 = u01f(r.c);
+  }
+  __device__ __forceinline__ float next() {
+    if (used >= 2) {
+      const U4 r = philox(U4{c0, c1, c2, ++blk}, k0, k1);
+      w0 = r.a; w2 = r.c; used = 0;
+    }
+    return u01f(used++ == 0 ? w0 : w2);
+  }
+};
+
+// id of the k-th secondary of the interaction at (parent id, parent step)
+__device__ __forceinline__ uint64_t child_id(uint32_t seed, uint32_t ev, uint64_t pid,
+                                             uint32_t pstep, uint32_t k) {
+  const U4 r = philox(U4{(uint32_t)pid, (uint32_t)(pid >> 32), pstep, 0x80000000u | k}, seed, ev);
+  return (uint64_t)r.a | ((uint64_t)r.b << 32);
+}
+
+// ---------------------------------------------------------------- tables
+template <class R> struct Grid {
+  static __device__ __forceinline__ R lnEmin() { return (R)kLnEmin; }
+  static __device__ __forceinline__ R invd() { return (R)kInvDlog; }
+  static __device__ __forceinline__ R dlog() { return (R)kDlog; }
+};
+
+// position of E on the grid: bin i in [0, NNODE-2] and fraction t
+template <class R>
+__device__ __forceinline__ void grid_pos(double E, int* i, R* t);
+
+template <>
+__device__ __forceinline__ void grid_pos<double>(double E, int* i, double* t) {
+  const double x = (::log(E) - kLnEmin) * kInvDlog;
+  int k = (int)::floor(x);
+  k = k < 0 ? 0 : (k > kNNode - 2 ? kNNode - 2 : k);
+  *i = k;
+  *t = x - (double)k;
+}
+
+// FP32 form: a float holds the grid coordinate (up to 288) only to ~2e-5, too coarse for
+// a 1e-6 lookup. With E = m 2^k, x = 96 + k * 32 log10(2) + ln(m) * 32/ln(10): the first
+// two terms are summed exactly (the product's rounding error is recovered with an FMA,
+// 32 log10 2 is split in two floats), so only ln(m) * 32/ln(10) < 9.7 carries float error.
+template <>
+__device__ __forceinline__ void grid_pos<float>(double E, int* i, float* t) {
+  const int bits = __float_as_int((float)E);
+  const float kf = (float)(((bits >> 23) & 0xFF) - 127);
+  const float m = __int_as_float((bits & 0x7FFFFF) | 0x3F800000);
+  const float c1_hi = 9.632960319519043f, c1_lo = -4.582716428558342e-07f;
+  const float p = kf * c1_hi;
+  const float e = fmaf(kf, c1_hi, -p);
+  const float q = 96.0f + p;
+  const float iq = floorf(q);
+  const float r = (q - iq) + (e + kf * c1_lo) + logf(m) * 13.89742374420166f;
+  const float fr = floorf(r);
+  int k = (int)iq + (int)fr;
+  float tt = r - fr;
+  if (k < 0) { tt += (float)k; k = 0; }
+  if (k > kNNode - 2) { tt += (float)(k - (kNNode - 2)); k = kNNode - 2; }
+  *i = k;
+  *t = tt;
+}
+
+template <class R> struct Pair2;
+template <> struct Pair2<double> { using T = double2; };
+template <> struct Pair2<float> { using T = float2; };
+
+// one interpolated entry of a (value, slope) record
+template <class R>
+__device__ __forceinline__ R lerp_rec(const typename Pair2<R>::T* rec, int j, R t) {
+  const typename Pair2<R>::T v = __ldg(rec + j);
+  return v.x + v.y * t;
+}
+
+// inverse of the piecewise linear-in-ln(E) range table: 0 below the first node
+template <class R>
+__device__ __forceinline__ double inverse_range(const R* nodes, R r, int hint_hi) {
+  if (!(r >= __ldg(nodes))) return 0.0;
+  int lo = 0, hi = hint_hi + 1;
+  if (hi > kNNode - 1) hi = kNNode - 1;
+  if (r >= __ldg(nodes + hi)) {
+    lo = hi;
+    hi = kNNode - 1;
+    if (r >= __ldg(nodes + hi)) return 1e6;
+  }
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(nodes + mid) <= r) lo = mid; else hi = mid;
+  }
+  const R a = __ldg(nodes + lo), b = __ldg(nodes + lo + 1);
+  const R t = (r - a) / (b - a);
+  return (double)M<R>::exp(Grid<R>::lnEmin() + ((R)lo + t) * Grid<R>::dlog());
+}
+
+// ---------------------------------------------------------------- direction helpers
+// express the local direction (sin t cos f, sin t sin f, cos t) about axis u globally
+template <class R>
+__device__ __forceinline__ void rotate_to(R ux, R uy, R uz, R cost, R phi, R* ox, R* oy, R* oz) {
+  R s2 = (R)1 - cost * cost;
+  s2 = s2 < (R)0 ? (R)0 : s2;
+  const R sint = M<R>::sqrt(s2);
+  R sp, cp;
+  M<R>::sincos(phi, &sp, &cp);
+  const R l0 = sint * cp, l1 = sint * sp, l2 = cost;
+  const R up2 = ux * ux + uy * uy;
+  if (up2 > (R)0) {
+    const R up = M<R>::sqrt(up2);
+    *ox = (ux * uz * l0 - uy * l1) / up + ux * l2;
+    *oy = (uy * uz * l0 + ux * l1) / up + uy * l2;
+    *oz = -up * l0 + uz * l2;
+  } else if (uz >= (R)0) {
+    *ox = l0; *oy = l1; *oz = l2;
+  } else {
+    *ox = -l0; *oy = l1; *oz = -l2;
+  }
+}
+
+template <class R>
+__device__ __forceinline__ void unit(R* x, R* y, R* z) {
+  const R n = M<R>::sqrt(*x * *x + *y * *y + *z * *z);
+  *x /= n; *y /= n; *z /= n;
+}
+
+// ---------------------------------------------------------------- interactions
+// Result of one discrete interaction: the parent's new state and up to two secondaries.
+template <class R> struct Ixn {
+  bool happened, parent_alive;
+  double parent_E;
+  R pd[3];
+  int n;
+  int sp[2];
+  double E[2];
+  R d[2][3];
+};
+
+constexpr int kMaxRej = 1000;
+
+// Compton scattering, Klein-Nishina, sampled by Butcher-Messel composition-rejection
+template <class R>
+__device__ void compton(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
+  const R kap = (R)(E / kMe);
+  const R e0 = (R)1 / ((R)1 + (R)2 * kap);
+  const R a1 = M<R>::log1p((R)2 * kap);
+  const R a2 = (R)0.5 * ((R)1 - e0 * e0);
+  R eps = 1, t = 0;
+  for (int it = 0; it < kMaxRej; ++it) {
+    const R r1 = st.next(), r2 = st.next(), r3 = st.next();
+    eps = (r1 * (a1 + a2) < a1) ? M<R>::exp(-a1 * r2) : M<R>::sqrt(e0 * e0 + ((R)1 - e0 * e0) * r2);
+    t = ((R)1 - eps) / (kap * eps);
+    const R g = (R)1 - eps * (t * ((R)2 - t)) / ((R)1 + eps * eps);
+    if (r3 < g) break;
+  }
+  const R phi = (R)(2.0 * kPi) * st.next();
+  const double Ep = (double)eps * E;
+  rotate_to<R>(u[0], u[1], u[2], (R)1 - t, phi, &r.pd[0], &r.pd[1], &r.pd[2]);
+  r.happened = true;
+  r.parent_alive = true;
+  r.parent_E = Ep;
+  r.n = 1;
+  r.sp[0] = 1;
+  r.E[0] = E - Ep;
+  const R Ef = (R)E, Epf = (R)Ep;
+  R px = Ef * u[0] - Epf * r.pd[0], py = Ef * u[1] - Epf * r.pd[1], pz = Ef * u[2] - Epf * r.pd[2];
+  unit<R>(&px, &py, &pz);
+  r.d[0][0] = px; r.d[0][1] = py; r.d[0][2] = pz;
+}
+
+// Bethe-Heitler pair: x = E+/E uniform on [m/E, 1 - m/E], accepted with 1 - 4/3 x(1-x)
+template <class R>
+__device__ void pair(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
+  r.happened = false;
+  if (!(E > 2.0 * kMe)) return;
+  const R a = (R)(kMe / E);
+  R x = (R)0.5;
+  for (int it = 0; it < kMaxRej; ++it) {
+    const R r1 = st.next(), r2 = st.next();
+    x = a + ((R)1 - (R)2 * a) * r1;
+    if (r2 < (R)1 - (R)(4.0 / 3.0) * x * ((R)1 - x)) break;
+  }
+  const double Tp = (double)x * E - kMe;
+  const double Tm = E - 2.0 * kMe - Tp;
+  const R phi = (R)(2.0 * kPi) * st.next();
+  r.happened = true;
+  r.parent_alive = false;
+  r.n = 2;
+  r.sp[0] = 2;
+  r.E[0] = Tp;
+  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)(kMe / (Tp + kMe))), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
+  r.sp[1] = 1;
+  r.E[1] = Tm;
+  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)(kMe / (Tm + kMe))), phi + (R)kPi, &r.d[1][0], &r.d[1][1], &r.d[1][2]);
+}
+
+template <class R>
+__device__ __forceinline__ void photo(double E, const R u[3], Ixn<R>& r) {
+  r.happened = true;
+  r.parent_alive = false;
+  r.n = 1;
+  r.sp[0] = 1;
+  r.E[0] = E;
+  r.d[0][0] = u[0]; r.d[0][1] = u[1]; r.d[0][2] = u[2];
+}
+
+// free-electron two-body kinematics of a delta ray of kinetic energy Td
+template <class R>
+__device__ void delta_ray(Stream<R>& st, double T, double Td, const R u[3], Ixn<R>& r) {
+  R cd = M<R>::sqrt((R)(Td * (T + 2.0 * kMe) / (T * (Td + 2.0 * kMe))));
+  cd = cd > (R)1 ? (R)1 : cd;
+  const R phi = (R)(2.0 * kPi) * st.next();
+  R dx, dy, dz;
+  rotate_to<R>(u[0], u[1], u[2], cd, phi, &dx, &dy, &dz);
+  const R p0 = M<R>::sqrt((R)(T * (T + 2.0 * kMe)));
+  const R pd = M<R>::sqrt((R)(Td * (Td + 2.0 * kMe)));
+  R px = p0 * u[0] - pd * dx, py = p0 * u[1] - pd * dy, pz = p0 * u[2] - pd * dz;
+  unit<R>(&px, &py, &pz);
+  r.happened = true;
+  r.parent_alive = true;
+  r.parent_E = T - Td;
+  r.pd[0] = px; r.pd[1] = py; r.pd[2] = pz;
+  r.n = 1;
+  r.sp[0] = 1;
+  r.E[0] = Td;
+  r.d[0][0] = dx; r.d[0][1] = dy; r.d[0][2] = dz;
+}
+
+// Moller: eps from 1/eps^2 on [Tc/T, 1/2], accepted with eps^2 f(eps) / (2 + (1-gg)/4)
+template <class R>
+__device__ void moller(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>& r) {
+  r.happened = false;
+  if (!(T > 2.0 * Tc)) return;
+  const R g = (R)(T / kMe + 1.0);
+  const R gg = ((R)2 * g - (R)1) / (g * g);
+  const R ec = (R)(Tc / T), em = (R)0.5;
+  const R gmax = (R)2 + (R)0.25 * ((R)1 - gg);
+  R eps = ec;
+  for (int it = 0; it < kMaxRej; ++it) {
+    const R r1 = st.next(), r2 = st.next();
+    eps = ec * em / (em - (em - ec) * r1);
+    const R q = eps / ((R)1 - eps);
+    const R f = (R)1 + q * q + ((R)1 - gg) * eps * eps - gg * q;
+    if (r2 * gmax < f) break;
+  }
+  delta_ray<R>(st, T, (double)eps * T, u, r);
+}
+
+// Bhabha: eps from 1/eps^2 on [Tc/T, 1], accepted with 1 - b2 eps (B1 - eps (B2 - eps (B3 - eps B4)))
+template <class R>
+__device__ void bhabha(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>& r) {
+  r.happened = false;
+  if (!(T > Tc)) return;
+  const R tau = (R)(T / kMe);
+  const R g = tau + (R)1;
+  const R b2 = tau * (tau + (R)2) / (g * g);
+  const R y = (R)1 / (g + (R)1);
+  const R y12 = (R)1 - (R)2 * y;
+  const R B1 = (R)2 - y * y, B2 = y12 * ((R)3 + y * y), B4 = y12 * y12 * y12;
+  const R B3 = B4 + y12 * y12;
+  const R ec = (R)(Tc / T);
+  R eps = ec;
+  for (int it = 0; it < kMaxRej; ++it) {
+    const R r1 = st.next(), r2 = st.next();
+    eps = ec / ((R)1 - ((R)1 - ec) * r1);
+    const R gf = (R)1 - b2 * eps * (B1 - eps * (B2 - eps * (B3 - eps * B4)));
+    if (r2 < gf) break;
+  }
+  delta_ray<R>(st, T, (double)eps * T, u, r);
+}
+
+// Tsai bremsstrahlung: k = kc (T/kc)^r, accepted with 1 - y + 3/4 y^2; photon at angle m/E
+template <class R>
+__device__ void brem(Stream<R>& st, double T, double kc, const R u[3], Ixn<R>& r) {
+  r.happened = false;
+  if (!(T > kc)) return;
+  const double E = T + kMe;
+  const R lr = M<R>::log((R)(T / kc));
+  const R kcR = (R)kc, Ef = (R)E;
+  R k = kcR;
+  for (int it = 0; it < kMaxRej; ++it) {
+    const R r1 = st.next(), r2 = st.next();
+    k = kcR * M<R>::exp(lr * r1);
+    const R y = k / Ef;
+    if (r2 < (R)1 - y + (R)0.75 * y * y) break;
+  }
+  double kd = (double)k;
+  if (kd > T) kd = T;  // FP32 rounding of kc (T/kc)^r can step past T
+  const R phi = (R)(2.0 * kPi) * st.next();
+  r.happened = true;
+  r.parent_alive = true;
+  r.parent_E = T - kd;
+  r.pd[0] = u[0]; r.pd[1] = u[1]; r.pd[2] = u[2];
+  r.n = 1;
+  r.sp[0] = 0;
+  r.E[0] = kd;
+  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)(kMe / E)), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
+}
+
+// Heitler annihilation in flight: eps = E1/(T+2m) from 1/eps on [eps_min, eps_max],
+// accepted with 1 - eps + (2 g eps - 1)/(eps (g+1)^2)
+template <class R>
+__device__ void annihilate(Stream<R>& st, double T, const R u[3], Ixn<R>& r) {
+  const R tau = (R)(T / kMe);
+  const R g = tau + (R)1;
+  const R sq = M<R>::sqrt(tau / (tau + (R)2));
+  const R emin = (R)0.5 * ((R)1 - sq), emax = (R)0.5 * ((R)1 + sq);
+  const R lr = M<R>::log(emax / emin);
+  const R gp1 = g + (R)1;
+  R eps = (R)0.5;
+  for (int it = 0; it < kMaxRej; ++it) {
+    const R r1 = st.next(), r2 = st.next();
+    eps = emin * M<R>::exp(lr * r1);
+    const R gf = (R)1 - eps + ((R)2 * g * eps - (R)1) / (eps * gp1 * gp1);
+    if (r2 < gf) break;
+  }
+  const double Etot = T + 2.0 * kMe;
+  const double E1 = (double)eps * Etot;
+  const double E2 = Etot - E1;
+  R c1 = (eps * gp1 - (R)1) / (eps * M<R>::sqrt(tau * (tau + (R)2)));
+  c1 = c1 > (R)1 ? (R)1 : (c1 < (R)-1 ? (R)-1 : c1);
+  const R phi = (R)(2.0 * kPi) * st.next();
+  r.happened = true;
+  r.parent_alive = false;
+  r.n = 2;
+  r.sp[0] = 0;
+  r.E[0] = E1;
+  rotate_to<R>(u[0], u[1], u[2], c1, phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
+  r.sp[1] = 0;
+  r.E[1] = E2;
+  const R pp = M<R>::sqrt((R)(T * (T + 2.0 * kMe)));
+  const R E1f = (R)E1;
+  R x = pp * u[0] - E1f * r.d[0][0], y = pp * u[1] - E1f * r.d[0][1], z = pp * u[2] - E1f * r.d[0][2];
+  unit<R>(&x, &y, &z);
+  r.d[1][0] = x; r.d[1][1] = y; r.d[1][2] = z;
+}
+
+template <class R>
+__device__ void annihilate_at_rest(Stream<R>& st, Ixn<R>& r) {
+  const R ct = (R)2 * st.next() - (R)1;
+  const R phi = (R)(2.0 * kPi) * st.next();
+  R s2 = (R)1 - ct * ct;
+  s2 = s2 < (R)0 ? (R)0 : s2;
+  const R s = M<R>::sqrt(s2);
+  R sp, cp;
+  M<R>::sincos(phi, &sp, &cp);
+  r.happened = true;
+  r.parent_alive = false;
+  r.n = 2;
+  r.sp[0] = 0; r.sp[1] = 0;
+  r.E[0] = kMe; r.E[1] = kMe;
+  r.d[0][0] = s * cp; r.d[0][1] = s * sp; r.d[0][2] = ct;
+  r.d[1][0] = -r.d[0][0]; r.d[1][1] = -r.d[0][1]; r.d[1][2] = -r.d[0][2];
+}
+
+// ---------------------------------------------------------------- geometry
+// Slab: volumes between planes bnd[0..n_vol] along z, |x|,|y| <= half_xy. Tubes: volume
+// 0 is r < bnd[0], volume v is bnd[v-1] <= r < bnd[v], |z| <= half_z. next = -1 leaves.
+template <class R>
+__device__ __forceinline__ R slab_wall(R p, R u, R H) {
+  return u > (R)0 ? (H - p) / u : (u < (R)0 ? (-H - p) / u : M<R>::big());
+}
+
+template <class R>
+__device__ double straight_distance(const GeoView& g, double x, double y, double z, const R u[3],
+                                    int vol, int* next) {
+  double s = kBig;
+  int nx = vol;
+  if (g.kind == 0) {
+    if (u[2] > (R)0) {
+      s = (double)((R)(__ldg(g.bnd + vol + 1) - z) / u[2]);
+      nx = (vol + 1 < g.n_vol) ? vol + 1 : -1;
+    } else if (u[2] < (R)0) {
+      s = (double)((R)(__ldg(g.bnd + vol) - z) / u[2]);
+      nx = vol - 1;
+    }
+    const R H = (R)g.half_xy;
+    const R sx = slab_wall<R>((R)x, u[0], H);
+    const R sy = slab_wall<R>((R)y, u[1], H);
+    if ((double)sx < s) { s = (double)sx; nx = -1; }
+    if ((double)sy < s) { s = (double)sy; nx = -1; }
+  } else {
+    const R a = u[0] * u[0] + u[1] * u[1];
+    const R b = (R)x * u[0] + (R)y * u[1];
+    const double r2 = x * x + y * y;
+    if (a > (R)0) {
+      const double Ro = __ldg(g.bnd + vol);
+      const R co = (R)(r2 - Ro * Ro);
+      R D = b * b - a * co;
+      D = D < (R)0 ? (R)0 : D;
+      const R sq = M<R>::sqrt(D);
+      R so = (b > (R)0) ? -co / (b + sq) : (sq - b) / a;
+      so = so < (R)0 ? (R)0 : so;
+      s = (double)so;
+      nx = (vol + 1 < g.n_vol) ? vol + 1 : -1;
+      if (vol > 0 && b < (R)0) {
+        const double Ri = __ldg(g.bnd + vol - 1);
+        const R ci = (R)(r2 - Ri * Ri);
+        const R Di = b * b - a * ci;
+        if (Di > (R)0) {
+          R si = ci / (M<R>::sqrt(Di) - b);
+          si = si < (R)0 ? (R)0 : si;
+          if ((double)si < s) { s = (double)si; nx = vol - 1; }
+        }
+      }
+    }
+    double sz = kBig;
+    if (u[2] > (R)0) sz = (double)((R)(g.half_z - z) / u[2]);
+    else if (u[2] < (R)0) sz = (double)((R)(-g.half_z - z) / u[2]);
+    if (sz < s) { s = sz; nx = -1; }
+  }
+  *next = nx;
+  return s < 0.0 ? 0.0 : s;
+}
+
+// Helix in B along z: h = -sign(qB) turns the transverse direction, rho = p_T/(K |B|),
+// the phase advances by Delta = s u_T / rho over a path s.
+template <class R> struct Helix {
+  bool straight;
+  R uT, rho, h, kpath;
+  double cx, cy;
+};
+
+template <class R>
+__device__ __forceinline__ void helix_setup(double B, double T, int q, const R u[3], double x, double y,
+                                            Helix<R>& H) {
+  H.straight = true;
+  if (B == 0.0 || q == 0) return;
+  const R uT = M<R>::sqrt(u[0] * u[0] + u[1] * u[1]);
+  if (!(uT > (R)1e-12)) return;
+  const R pm = M<R>::sqrt((R)(T * (T + 2.0 * kMe)));
+  H.straight = false;
+  H.uT = uT;
+  H.rho = pm * uT / (R)(kHelixK * fabs(B));
+  H.h = ((q > 0) == (B > 0.0)) ? (R)-1 : (R)1;
+  H.cx = x - (double)(H.rho * H.h * u[1] / uT);
+  H.cy = y + (double)(H.rho * H.h * u[0] / uT);
+  H.kpath = uT / H.rho;
+}
+
+template <class R>
+__device__ __forceinline__ R wrap2pi(R x) {
+  const R tp = (R)(2.0 * kPi);
+  R r = M<R>::fmod(x, tp);
+  if (r < (R)0) r += tp;
+  if (r > tp - M<R>::turn_tol()) r = (R)0;
+  return r;
+}
+
+// first crossing in the asked direction of a level set whose crossings sit at phase
+// psi_ref -/+ acos(C) on the circle; dpsi = psi_ref - psi0 is passed in directly
+template <class R>
+__device__ __forceinline__ double helix_hit(const Helix<R>& H, R dpsi, R C, bool increasing) {
+  if (!(C >= (R)-1 && C <= (R)1)) return kBig;
+  const R A = M<R>::acos(C);
+  const R base = H.h * dpsi;
+  const R D = wrap2pi<R>(increasing ? base - A : base + A);
+  return (double)(D / H.kpath);
+}
+
+// phase of direction (ax, ay) minus the particle's phase psi0, in (-pi, pi]
+template <class R>
+__device__ __forceinline__ R phase_from(const Helix<R>& H, const R u[3], R ax, R ay) {
+  // unit radial vector of the particle: (cos psi0, sin psi0) = (h uy, -h ux) / uT
+  const R c0 = H.h * u[1] / H.uT, s0 = -H.h * u[0] / H.uT;
+  return M<R>::atan2(c0 * ay - s0 * ax, c0 * ax + s0 * ay);
+}
+
+template <class R>
+__device__ double helix_distance(const GeoView& g, double B, double T, int q, double x, double y,
+                                 double z, const R u[3], int vol, int* next) {
+  Helix<R> H;
+  helix_setup<R>(B, T, q, u, x, y, H);
+  if (H.straight) return straight_distance<R>(g, x, y, z, u, vol, next);
+  double s = kBig;
+  int nx = vol;
+  if (g.kind == 0) {
+    if (u[2] > (R)0) {
+      s = (double)((R)(__ldg(g.bnd + vol + 1) - z) / u[2]);
+      nx = (vol + 1 < g.n_vol) ? vol + 1 : -1;
+    } else if (u[2] < (R)0) {
+      s = (double)((R)(__ldg(g.bnd + vol) - z) / u[2]);
+      nx = vol - 1;
+    }
+    const double Hw = g.half_xy;
+    if (!(fabs(H.cx) + (double)H.rho < Hw && fabs(H.cy) + (double)H.rho < Hw)) {
+      // walls +x, -x, +y, -y as n.P = Hw, crossed outward
+      const R nxs[4] = {(R)1, (R)-1, (R)0, (R)0}, nys[4] = {(R)0, (R)0, (R)1, (R)-1};
+      const double nc[4] = {H.cx, -H.cx, H.cy, -H.cy};
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const double sw = helix_hit<R>(H, phase_from<R>(H, u, nxs[w], nys[w]), (R)((Hw - nc[w]) / (double)H.rho), true);
+        if (sw < s) { s = sw; nx = -1; }
+      }
+    }
+  } else {
+    const double cm2 = H.cx * H.cx + H.cy * H.cy;
+    const R cm = M<R>::sqrt((R)cm2);
+    if (cm > (R)1e-12) {
+      const R dpsi = phase_from<R>(H, u, (R)H.cx, (R)H.cy);
+      const double rho2 = (double)H.rho * (double)H.rho;
+      const R den = (R)2 * H.rho * cm;
+      const double Ro = __ldg(g.bnd + vol);
+      const double so = helix_hit<R>(H, dpsi, (R)(Ro * Ro - cm2 - rho2) / den, true);
+      if (so < s) { s = so; nx = (vol + 1 < g.n_vol) ? vol + 1 : -1; }
+      if (vol > 0) {
+        const double Ri = __ldg(g.bnd + vol - 1);
+        const double si = helix_hit<R>(H, dpsi, (R)(Ri * Ri - cm2 - rho2) / den, false);
+        if (si < s) { s = si; nx = vol - 1; }
+      }
+    }
+    double sz = kBig;
+    if (u[2] > (R)0) sz = (double)((R)(g.half_z - z) / u[2]);
+    else if (u[2] < (R)0) sz = (double)((R)(-g.half_z - z) / u[2]);
+    if (sz < s) { s = sz; nx = -1; }
+    if (s >= kBig) { s = (double)((R)(2.0 * kPi) / H.kpath); nx = vol; }  // closed circle: one turn
+  }
+  *next = nx;
+  return s;
+}
+
+// move along the helix (or straight) by s; position stays double, direction in R
+template <class R>
+__device__ __forceinline__ void helix_move(double B, double T, int q, double s, double* x, double* y,
+                                           double* z, R u[3]) {
+  Helix<R> H;
+  helix_setup<R>(B, T, q, u, *x, *y, H);
+  if (H.straight) {
+    *x += s * (double)u[0]; *y += s * (double)u[1]; *z += s * (double)u[2];
+    return;
+  }
+  const R D = (R)s * H.kpath;
+  R sd, cd;
+  M<R>::sincos(D, &sd, &cd);
+  const R sh = M<R>::sin((R)0.5 * D);
+  const R cm1 = (R)-2 * sh * sh;
+  const R a = u[0] / H.uT, b = u[1] / H.uT;
+  *x += (double)(H.rho * (a * sd + H.h * b * cm1));
+  *y += (double)(H.rho * (b * sd - H.h * a * cm1));
+  *z += s * (double)u[2];
+  const R u0 = u[0] * cd - H.h * u[1] * sd;
+  const R u1 = u[1] * cd + H.h * u[0] * sd;
+  u[0] = u0; u[1] = u1;
+}
+
+// locate a point: on a surface, the volume the direction points into
+__device__ __forceinline__ int locate(const GeoView& g, double x, double y, double z, double ux, double uy,
+                                      double uz) {
+  if (g.kind == 0) {
+    if (fabs(x) > g.half_xy || fabs(y) > g.half_xy) return -1;
+    if (z < g.bnd[0] || z > g.bnd[g.n_vol]) return -1;
+    int lo = 0, hi = g.n_vol;  // find k with bnd[k] <= z < bnd[k+1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (g.bnd[mid] <= z) lo = mid; else hi = mid;
+    }
+    if (z == g.bnd[g.n_vol]) lo = g.n_vol;
+    if (z == g.bnd[lo]) {
+      const int v = uz >= 0.0 ? lo : lo - 1;
+      return (v < 0 || v >= g.n_vol) ? -1 : v;
+    }
+    return lo;
+  }
+  if (fabs(z) > g.half_z) return -1;
+  const double r = sqrt(x * x + y * y);
+  const double radial = x * ux + y * uy;
+  int v = 0;
+  for (int k = 0; k < g.n_vol; ++k) {
+    const double b = g.bnd[k];
+    if (fabs(r - b) <= 1e-9 * b) {
+      v = radial > 0.0 ? k + 1 : k;
+      return v >= g.n_vol ? -1 : v;
+    }
+    if (b < r) v = k + 1;
+  }
+  return v >= g.n_vol ? -1 : v;
+}
+
+}  // namespace adept

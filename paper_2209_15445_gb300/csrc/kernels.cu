@@ -1,0 +1,743 @@
+// Kernels of the shower transport: table build, the per-generation step kernel over
+// the three species queues, primary injection, event completion, and parity probes.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "layout.h"
+#include "physics_init.cuh"
+
+namespace adept {
+
+// ======================================================================== table build
+// raw value rows in BuildScratch::vals
+enum { V_MUC, V_MUP, V_MUPH, V_SFULL, V_SE, V_IE, V_BE, V_SP, V_IP, V_BP, V_AP, V_RFULL, V_RE, V_RP, V_NROW };
+enum { B_RFULL, B_RE, B_RP };
+
+__device__ inline double node_E(int i) { return exp(kLnEmin + (double)i * kDlog); }
+
+__global__ void k_materials(const double* in, int n, MatDev* out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < n) init::setup_material(in + 4 * m, out + m);
+}
+
+__device__ inline double s_full(const MatDev& M, double T) {
+  return init::dedx_col(M, T, T, false) + init::dedx_rad(M, T, T);
+}
+__device__ inline double s_restr(const MatDev& M, double T, double Tc, double kc, bool pos) {
+  return init::dedx_col(M, T, Tc, pos) + init::dedx_rad(M, T, kc);
+}
+
+// Simpson rule with 8 panels of T/S(T) over bin i in ln T
+template <class F>
+__device__ inline double bin_integral(int i, F S) {
+  const double h = kDlog / 8.0;
+  double acc = 0.0;
+  for (int j = 0; j <= 8; ++j) {
+    const double T = exp(kLnEmin + (double)i * kDlog + (double)j * h);
+    const double w = (j == 0 || j == 8) ? 1.0 : ((j & 1) ? 4.0 : 2.0);
+    acc += w * (T / S(T));
+  }
+  return acc * h / 3.0;
+}
+
+__global__ void k_gamma_full(const MatDev* mats, int n_mat, BuildScratch s) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_mat * kNNode) return;
+  const int m = idx / kNNode, i = idx % kNNode;
+  const MatDev M = mats[m];
+  if (M.vacuum) return;
+  double* v = s.vals + (size_t)m * V_NROW * kNNode;
+  const double E = node_E(i);
+  v[V_MUC * kNNode + i] = init::mu_compton(M, E);
+  v[V_MUP * kNNode + i] = init::mu_pair(M, E);
+  v[V_MUPH * kNNode + i] = init::mu_photo(M, E);
+  v[V_SFULL * kNNode + i] = s_full(M, E);
+  if (i < kNNode - 1)
+    s.bins[((size_t)m * 3 + B_RFULL) * kNNode + i] = bin_integral(i, [&](double T) { return s_full(M, T); });
+}
+
+__device__ inline double clamp_cut(double x) { return x < 0.99e-3 ? 0.99e-3 : (x > 1e4 ? 1e4 : x); }
+
+// range of a stopping-power row: R(E0) = E0/(2 S(E0)) (S taken as 1/T below the grid),
+// then the running sum of the bin integrals
+__device__ inline void prefix_range(const double* S, const double* bins, double* R) {
+  double r = node_E(0) / (2.0 * S[0]);
+  R[0] = r;
+  for (int i = 0; i < kNNode - 1; ++i) {
+    r += bins[i];
+    R[i + 1] = r;
+  }
+}
+
+// production thresholds: e+- from the unrestricted range, gamma from 5 mean free paths
+__global__ void k_cuts(const MatDev* mats, int n_mat, double range_cut, BuildScratch s, double* Tc, double* kc) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n_mat) return;
+  if (mats[m].vacuum) { Tc[m] = 0.0; kc[m] = 0.0; return; }
+  double* v = s.vals + (size_t)m * V_NROW * kNNode;
+  double* Rf = v + V_RFULL * kNNode;
+  prefix_range(v + V_SFULL * kNNode, s.bins + ((size_t)m * 3 + B_RFULL) * kNNode, Rf);
+  double t_c = 1e6;
+  if (range_cut <= Rf[0]) {
+    t_c = node_E(0);
+  } else {
+    for (int i = 0; i < kNNode - 1; ++i)
+      if (Rf[i + 1] >= range_cut) {
+        const double t = (range_cut - Rf[i]) / (Rf[i + 1] - Rf[i]);
+        t_c = exp(kLnEmin + ((double)i + t) * kDlog);
+        break;
+      }
+  }
+  const double target = 5.0 / range_cut;
+  auto mu = [&](int i) { return v[V_MUC * kNNode + i] + v[V_MUP * kNNode + i] + v[V_MUPH * kNNode + i]; };
+  double k_c = 1e6;
+  if (mu(0) <= target) {
+    k_c = node_E(0);
+  } else {
+    for (int i = 0; i < kNNode - 1; ++i)
+      if (mu(i + 1) <= target) {
+        const double a = mu(i), b = mu(i + 1);
+        const double t = (a - target) / (a - b);
+        k_c = exp(kLnEmin + ((double)i + t) * kDlog);
+        break;
+      }
+  }
+  Tc[m] = clamp_cut(t_c);
+  kc[m] = clamp_cut(k_c);
+}
+
+__global__ void k_charged(const MatDev* mats, int n_mat, BuildScratch s, const double* Tc, const double* kc) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_mat * kNNode) return;
+  const int m = idx / kNNode, i = idx % kNNode;
+  const MatDev M = mats[m];
+  if (M.vacuum) return;
+  const double tc = Tc[m], kk = kc[m];
+  double* v = s.vals + (size_t)m * V_NROW * kNNode;
+  const double T = node_E(i);
+  v[V_SE * kNNode + i] = s_restr(M, T, tc, kk, false);
+  v[V_IE * kNNode + i] = init::lambda_ioni(M, T, tc, false);
+  v[V_BE * kNNode + i] = init::lambda_brem(M, T, kk);
+  v[V_SP * kNNode + i] = s_restr(M, T, tc, kk, true);
+  v[V_IP * kNNode + i] = init::lambda_ioni(M, T, tc, true);
+  v[V_BP * kNNode + i] = init::lambda_brem(M, T, kk);
+  v[V_AP * kNNode + i] = init::lambda_annih(M, T);
+  if (i < kNNode - 1) {
+    s.bins[((size_t)m * 3 + B_RE) * kNNode + i] = bin_integral(i, [&](double x) { return s_restr(M, x, tc, kk, false); });
+    s.bins[((size_t)m * 3 + B_RP) * kNNode + i] = bin_integral(i, [&](double x) { return s_restr(M, x, tc, kk, true); });
+  }
+}
+
+__global__ void k_ranges(const MatDev* mats, int n_mat, BuildScratch s) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 2 * n_mat) return;
+  const int m = idx >> 1, pos = idx & 1;
+  if (mats[m].vacuum) return;
+  double* v = s.vals + (size_t)m * V_NROW * kNNode;
+  prefix_range(v + (pos ? V_SP : V_SE) * kNNode, s.bins + ((size_t)m * 3 + (pos ? B_RP : B_RE)) * kNNode,
+               v + (pos ? V_RP : V_RE) * kNNode);
+}
+
+struct PackOut {
+  double2 *g64, *e64, *p64;
+  float2 *g32, *e32, *p32;
+  double *re64, *rp64;
+  float *re32, *rp32;
+};
+
+__device__ inline void put(double2* d64, float2* d32, size_t at, const double* row, int i) {
+  const double a = row[i];
+  const double b = (i + 1 < kNNode) ? row[i + 1] : row[i];
+  d64[at] = make_double2(a, b - a);
+  d32[at] = make_float2((float)a, (float)(b - a));
+}
+
+__global__ void k_pack(const MatDev* mats, int n_mat, BuildScratch s, PackOut o) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_mat * kNNode) return;
+  const int m = idx / kNNode, i = idx % kNNode;
+  const size_t r = (size_t)m * kNNode + i;
+  if (mats[m].vacuum) {
+    for (int t = 0; t < kNTabG; ++t) { o.g64[r * kNTabG + t] = make_double2(0, 0); o.g32[r * kNTabG + t] = make_float2(0, 0); }
+    for (int t = 0; t < kNTabE; ++t) { o.e64[r * kNTabE + t] = make_double2(0, 0); o.e32[r * kNTabE + t] = make_float2(0, 0); }
+    for (int t = 0; t < kNTabP; ++t) { o.p64[r * kNTabP + t] = make_double2(0, 0); o.p32[r * kNTabP + t] = make_float2(0, 0); }
+    o.re64[r] = o.rp64[r] = 0.0;
+    o.re32[r] = o.rp32[r] = 0.0f;
+    return;
+  }
+  const double* v = s.vals + (size_t)m * V_NROW * kNNode;
+  const int grow[kNTabG] = {V_MUC, V_MUP, V_MUPH};
+  const int erow[kNTabE] = {V_SE, V_RE, V_IE, V_BE};
+  const int prow[kNTabP] = {V_SP, V_RP, V_IP, V_BP, V_AP};
+  for (int t = 0; t < kNTabG; ++t) put(o.g64, o.g32, r * kNTabG + t, v + grow[t] * kNNode, i);
+  for (int t = 0; t < kNTabE; ++t) put(o.e64, o.e32, r * kNTabE + t, v + erow[t] * kNNode, i);
+  for (int t = 0; t < kNTabP; ++t) put(o.p64, o.p32, r * kNTabP + t, v + prow[t] * kNNode, i);
+  o.re64[r] = v[V_RE * kNNode + i];
+  o.rp64[r] = v[V_RP * kNNode + i];
+  o.re32[r] = (float)v[V_RE * kNNode + i];
+  o.rp32[r] = (float)v[V_RP * kNNode + i];
+}
+
+cudaError_t launch_build_tables(const Params& P, const double* mat_in, int n_mat, double range_cut, MatDev* mat,
+                                BuildScratch s, double2* g64, double2* e64, double2* p64, float2* g32,
+                                float2* e32, float2* p32, double* re64, double* rp64, float* re32, float* rp32,
+                                double* Tc, double* kc, cudaStream_t st) {
+  (void)P;
+  const int nn = n_mat * kNNode;
+  const int B = 128;
+  k_materials<<<1, 32, 0, st>>>(mat_in, n_mat, mat);
+  k_gamma_full<<<(nn + B - 1) / B, B, 0, st>>>(mat, n_mat, s);
+  k_cuts<<<1, 32, 0, st>>>(mat, n_mat, range_cut, s, Tc, kc);
+  k_charged<<<(nn + B - 1) / B, B, 0, st>>>(mat, n_mat, s, Tc, kc);
+  k_ranges<<<1, 32, 0, st>>>(mat, n_mat, s);
+  PackOut o{g64, e64, p64, g32, e32, p32, re64, rp64, re32, rp32};
+  k_pack<<<(nn + B - 1) / B, B, 0, st>>>(mat, n_mat, s, o);
+  return cudaGetLastError();
+}
+
+// ======================================================================== transport
+template <class R> struct Trk {
+  double x, y, z;
+  R u[3];
+  double E;
+  unsigned long long id;
+  uint32_t ev, step, nav;
+};
+
+template <class R>
+__device__ __forceinline__ void load_track(const TrackSoA& q, uint32_t i, Trk<R>& t) {
+  t.x = q.x[i]; t.y = q.y[i]; t.z = q.z[i];
+  t.u[0] = static_cast<const R*>(q.ux)[i];
+  t.u[1] = static_cast<const R*>(q.uy)[i];
+  t.u[2] = static_cast<const R*>(q.uz)[i];
+  t.E = q.E[i];
+  t.id = q.id[i];
+  t.ev = q.ev[i];
+  t.step = q.step[i];
+  t.nav = q.nav[i];
+}
+
+template <class R>
+__device__ __forceinline__ void store_track(const TrackSoA& q, uint32_t i, double x, double y, double z, R ux,
+                                            R uy, R uz, double E, unsigned long long id, uint32_t ev,
+                                            uint32_t step, uint32_t nav) {
+  q.x[i] = x; q.y[i] = y; q.z[i] = z;
+  static_cast<R*>(q.ux)[i] = ux;
+  static_cast<R*>(q.uy)[i] = uy;
+  static_cast<R*>(q.uz)[i] = uz;
+  q.E[i] = E;
+  q.id[i] = id;
+  q.ev[i] = ev;
+  q.step[i] = step;
+  q.nav[i] = nav;
+}
+
+template <class R> __device__ __forceinline__ const typename Pair2<R>::T* tab_g(const TableView& T);
+template <> __device__ __forceinline__ const double2* tab_g<double>(const TableView& T) { return T.g64; }
+template <> __device__ __forceinline__ const float2* tab_g<float>(const TableView& T) { return T.g32; }
+template <class R> __device__ __forceinline__ const typename Pair2<R>::T* tab_e(const TableView& T);
+template <> __device__ __forceinline__ const double2* tab_e<double>(const TableView& T) { return T.e64; }
+template <> __device__ __forceinline__ const float2* tab_e<float>(const TableView& T) { return T.e32; }
+template <class R> __device__ __forceinline__ const typename Pair2<R>::T* tab_p(const TableView& T);
+template <> __device__ __forceinline__ const double2* tab_p<double>(const TableView& T) { return T.p64; }
+template <> __device__ __forceinline__ const float2* tab_p<float>(const TableView& T) { return T.p32; }
+template <class R> __device__ __forceinline__ const R* range_nodes(const TableView& T, bool pos);
+template <> __device__ __forceinline__ const double* range_nodes<double>(const TableView& T, bool pos) { return pos ? T.rp64 : T.re64; }
+template <> __device__ __forceinline__ const float* range_nodes<float>(const TableView& T, bool pos) { return pos ? T.rp32 : T.re32; }
+
+__device__ __forceinline__ bool on(uint32_t mask, uint32_t bit) { return mask == 0u || (mask & bit); }
+
+// One step of one track of species S (0 gamma, 1 e-, 2 e+) -- paper Sec. 3: every live
+// track advances by one step per generation. On return: alive = the track goes to the
+// next queue of its species with state t; sec holds up to two secondaries (sp < 0 for
+// one deposited below the tracking cut); dep is the energy to score in bin dep_bin.
+template <class R, int S>
+__device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& alive, Ixn<R>& sec, double& dep,
+                                           int& dep_bin, uint32_t& pstep) {
+  constexpr int q = S == 1 ? -1 : (S == 2 ? 1 : 0);
+  const double rest = S == 2 ? 2.0 * kMe : 0.0;
+  const int vol = (int)(t.nav & 0xFFFFu);
+  uint32_t vac = t.nav >> 16;
+  const int m = __ldg(P.geo.vol_mat + vol);
+  dep_bin = __ldg(P.geo.vol_bin + vol);
+  alive = false;
+  sec.n = 0;
+  dep = 0.0;
+  const uint32_t step = t.step;
+  pstep = step;
+  if (step >= P.max_steps) { atomicAdd(P.evt.killed + t.ev, t.E + rest); return; }
+  if (m < 0) {
+    if (vac >= P.max_vac) { atomicAdd(P.evt.killed + t.ev, t.E + rest); return; }
+    ++vac;
+  } else {
+    vac = 0;
+  }
+  Stream<R> rs(P.seed, __ldg(P.evt.key + t.ev), t.id, step);
+  if (t.E < P.tcut) {
+    dep = t.E;
+    if (S == 2) annihilate_at_rest<R>(rs, sec);
+    return;
+  }
+  R u0, u1;
+  rs.block0(&u0, &u1);
+
+  // S2: cross sections and range at the pre-step energy
+  R sg0 = 0, sg1 = 0, sg2 = 0, Rr = 0;
+  int bin = 0;
+  if (m >= 0) {
+    R tt;
+    grid_pos<R>(t.E, &bin, &tt);
+    if (S == 0) {
+      const auto* rec = tab_g<R>(P.tab) + ((size_t)m * kNNode + bin) * kNTabG;
+      if (on(P.process_mask, 1u << 0)) sg0 = lerp_rec<R>(rec, 0, tt);
+      if (on(P.process_mask, 1u << 1)) sg1 = lerp_rec<R>(rec, 1, tt);
+      if (on(P.process_mask, 1u << 2)) sg2 = lerp_rec<R>(rec, 2, tt);
+    } else if (S == 1) {
+      const auto* rec = tab_e<R>(P.tab) + ((size_t)m * kNNode + bin) * kNTabE;
+      Rr = lerp_rec<R>(rec, 1, tt);
+      if (on(P.process_mask, 1u << 3)) sg0 = lerp_rec<R>(rec, 2, tt);
+      if (on(P.process_mask, 1u << 4)) sg1 = lerp_rec<R>(rec, 3, tt);
+    } else {
+      const auto* rec = tab_p<R>(P.tab) + ((size_t)m * kNNode + bin) * kNTabP;
+      Rr = lerp_rec<R>(rec, 1, tt);
+      if (on(P.process_mask, 1u << 5)) sg0 = lerp_rec<R>(rec, 2, tt);
+      if (on(P.process_mask, 1u << 6)) sg1 = lerp_rec<R>(rec, 3, tt);
+      if (on(P.process_mask, 1u << 7)) sg2 = lerp_rec<R>(rec, 4, tt);
+    }
+  }
+  sg0 = sg0 < (R)0 ? (R)0 : sg0;
+  sg1 = sg1 < (R)0 ? (R)0 : sg1;
+  sg2 = sg2 < (R)0 ? (R)0 : sg2;
+  const R stot = sg0 + sg1 + sg2;
+  // S3/S4: sampled interaction length and the range-based step limit
+  double s_phys = stot > (R)0 ? (double)(-M<R>::log(u0) / stot) : kBig;
+  if (q != 0 && m >= 0) {
+    const R smax = (Rr <= (R)kRhoF) ? Rr : ((R)kAlphaR * Rr > (R)kRhoF ? (R)kAlphaR * Rr : (R)kRhoF);
+    if ((double)smax < s_phys) s_phys = (double)smax;
+  }
+  // S5/S6: distance to the boundary along the straight line or helix
+  int next;
+  const bool field = (q != 0) && (P.field_T != 0.0);
+  const double s_geom = field ? helix_distance<R>(P.geo, P.field_T, t.E, q, t.x, t.y, t.z, t.u, vol, &next)
+                              : straight_distance<R>(P.geo, t.x, t.y, t.z, t.u, vol, &next);
+  const bool boundary = s_geom <= s_phys;
+  const double s = boundary ? s_geom : s_phys;
+  if (field) {
+    helix_move<R>(P.field_T, t.E, q, s, &t.x, &t.y, &t.z, t.u);
+  } else {
+    t.x += s * (double)t.u[0]; t.y += s * (double)t.u[1]; t.z += s * (double)t.u[2];
+  }
+  if (boundary && P.geo.kind == 0 && next >= 0) t.z = __ldg(P.geo.bnd + (t.u[2] > (R)0 ? vol + 1 : vol));
+  t.step = step + 1;
+
+  // S7: continuous loss by inverting the range table
+  if (q != 0 && m >= 0) {
+    double Ep = 0.0;
+    if ((R)s < Rr) Ep = inverse_range<R>(range_nodes<R>(P.tab, S == 2) + (size_t)m * kNNode, Rr - (R)s, bin + 1);
+    if (Ep > t.E) Ep = t.E;
+    dep += t.E - Ep;
+    t.E = Ep;
+    if (t.E < P.tcut) {
+      dep += t.E;
+      t.E = 0.0;
+      if (S == 2) annihilate_at_rest<R>(rs, sec);
+      return;
+    }
+  }
+  // S8: boundary crossing
+  if (boundary) {
+    if (next < 0) { atomicAdd(P.evt.leaked + t.ev, t.E + rest); return; }
+    t.nav = (uint32_t)next | (vac << 16);
+    alive = true;
+    return;
+  }
+  t.nav = (uint32_t)vol | (vac << 16);
+  // S9: discrete interaction, process chosen with u1 over the fixed order
+  const R xs = u1 * stot;
+  int proc = (S == 1) ? 1 : 2;
+  if (xs < sg0) proc = 0;
+  else if (xs < sg0 + sg1) proc = 1;
+  const double Tc = __ldg(P.tab.Tc + m), kc = __ldg(P.tab.kc + m);
+  sec.happened = false;
+  if (S == 0) {
+    if (proc == 0) compton<R>(rs, t.E, t.u, sec);
+    else if (proc == 1) pair<R>(rs, t.E, t.u, sec);
+    else photo<R>(t.E, t.u, sec);
+  } else if (S == 1) {
+    if (proc == 0) moller<R>(rs, t.E, Tc, t.u, sec);
+    else brem<R>(rs, t.E, kc, t.u, sec);
+  } else {
+    if (proc == 0) bhabha<R>(rs, t.E, Tc, t.u, sec);
+    else if (proc == 1) brem<R>(rs, t.E, kc, t.u, sec);
+    else annihilate<R>(rs, t.E, t.u, sec);
+  }
+  if (!sec.happened) { sec.n = 0; alive = true; return; }
+  // secondaries other than positrons below the tracking cut deposit locally
+  for (int k = 0; k < sec.n; ++k)
+    if (sec.sp[k] != 2 && sec.E[k] < P.tcut) { dep += sec.E[k]; sec.sp[k] = -1; }
+  if (!sec.parent_alive) return;
+  t.E = sec.parent_E;
+  t.u[0] = sec.pd[0]; t.u[1] = sec.pd[1]; t.u[2] = sec.pd[2];
+  if (S == 0 && t.E < P.tcut) { dep += t.E; return; }
+  alive = true;
+}
+
+constexpr int kMaxWarps = 32;
+
+struct StepShared {
+  uint32_t n[3];
+  uint32_t wc[kMaxWarps][3];
+  uint32_t woff[kMaxWarps][3];
+  uint32_t base[3];
+  unsigned long long steps[3], created[3];
+};
+
+template <class R, int S>
+__device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, StepShared& sh) {
+  const uint32_t i = base + threadIdx.x;
+  const bool active = i < sh.n[S];
+  Trk<R> t;
+  bool alive = false;
+  Ixn<R> sec;
+  sec.n = 0;
+  double dep = 0.0;
+  int dep_bin = -1;
+  uint32_t pstep = 0;
+  if (active) {
+    load_track<R>(P.q[p][S], i, t);
+    step_track<R, S>(P, t, alive, sec, dep, dep_bin, pstep);
+    // S10: score the step's deposit in (event, layer, material)
+    if (dep != 0.0 && dep_bin >= 0) atomicAdd(P.evt.edep + (size_t)t.ev * P.geo.n_bins + dep_bin, dep);
+  }
+  // S9/S11: warp-aggregated, then block-aggregated appends to the next queues
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const bool f1 = active && sec.n > 0 && sec.sp[0] >= 0;
+  const bool f2 = active && sec.n > 1 && sec.sp[1] >= 0;
+  const int s1 = f1 ? sec.sp[0] : -1, s2 = f2 ? sec.sp[1] : -1;
+  uint32_t b0[3], b1[3], b2[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    b0[k] = __ballot_sync(0xFFFFFFFFu, alive && k == S);
+    b1[k] = __ballot_sync(0xFFFFFFFFu, s1 == k);
+    b2[k] = __ballot_sync(0xFFFFFFFFu, s2 == k);
+  }
+  const uint32_t act = __ballot_sync(0xFFFFFFFFu, active);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sh.wc[warp][k] = __popc(b0[k]) + __popc(b1[k]) + __popc(b2[k]);
+    atomicAdd(&sh.steps[S], (unsigned long long)__popc(act));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) atomicAdd(&sh.created[k], (unsigned long long)(__popc(b1[k]) + __popc(b2[k])));
+  }
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (threadIdx.x < 3) {
+    const int k = threadIdx.x;
+    uint32_t acc = 0;
+    for (int w = 0; w < nw; ++w) { sh.woff[w][k] = acc; acc += sh.wc[w][k]; }
+    sh.base[k] = acc ? atomicAdd(&P.ctrl->count[p ^ 1][k], acc) : 0u;
+  }
+  __syncthreads();
+  const TrackSoA* nq = P.q[p ^ 1];
+  if (alive) {
+    const uint32_t d = sh.base[S] + sh.woff[warp][S] + __popc(b0[S] & lt);
+    if (d < P.cap) {
+      store_track<R>(nq[S], d, t.x, t.y, t.z, t.u[0], t.u[1], t.u[2], t.E, t.id, t.ev, t.step, t.nav);
+    } else {
+      atomicAdd(&P.ctrl->overflow, 1ull);
+      atomicAdd(P.evt.killed + t.ev, t.E + (S == 2 ? 2.0 * kMe : 0.0));
+    }
+  }
+  const uint32_t vnav = t.nav & 0xFFFFu;  // secondaries start with no vacuum history
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int sk = k == 0 ? s1 : s2;
+    if (sk < 0) continue;
+    const uint32_t before = __popc(b0[sk]) + (k == 1 ? __popc(b1[sk]) : 0u);
+    const uint32_t mine = __popc((k == 0 ? b1[sk] : b2[sk]) & lt);
+    const uint32_t d = sh.base[sk] + sh.woff[warp][sk] + before + mine;
+    if (d < P.cap) {
+      const unsigned long long cid = child_id(P.seed, __ldg(P.evt.key + t.ev), t.id, pstep, (uint32_t)k);
+      store_track<R>(nq[sk], d, t.x, t.y, t.z, sec.d[k][0], sec.d[k][1], sec.d[k][2], sec.E[k], cid, t.ev, 0u,
+                     vnav);
+    } else {
+      atomicAdd(&P.ctrl->overflow, 1ull);
+      atomicAdd(P.evt.killed + t.ev, sec.E[k] + (sk == 2 ? 2.0 * kMe : 0.0));
+    }
+  }
+  __syncthreads();
+}
+
+// One generation for all three species (paper Sec. 3: the three per-species transport
+// kernels; here one persistent launch whose blocks take tiles of the e-, e+ and gamma
+// queues). The last block to finish publishes the next queue sizes and advances gen.
+template <class R>
+__global__ void __launch_bounds__(256) k_step(Params P) {
+  __shared__ StepShared sh;
+  const uint32_t gen = __ldcg(&P.ctrl->gen);
+  const int p = gen & 1;
+  if (threadIdx.x < 3) {
+    // injection may have counted past the capacity (those tracks were dropped)
+    const uint32_t n = __ldcg(&P.ctrl->count[p][threadIdx.x]);
+    sh.n[threadIdx.x] = n < P.cap ? n : P.cap;
+    sh.steps[threadIdx.x] = 0;
+    sh.created[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  const uint32_t B = blockDim.x;
+  const uint32_t te = (sh.n[1] + B - 1) / B, tp = (sh.n[2] + B - 1) / B, tg = (sh.n[0] + B - 1) / B;
+  const uint32_t total = te + tp + tg;
+  for (uint32_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    if (tile < te) run_tile<R, 1>(P, p, tile * B, sh);
+    else if (tile < te + tp) run_tile<R, 2>(P, p, (tile - te) * B, sh);
+    else run_tile<R, 0>(P, p, (tile - te - tp) * B, sh);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) {
+      if (sh.steps[k]) atomicAdd(&P.ctrl->steps[k], sh.steps[k]);
+      if (sh.created[k]) atomicAdd(&P.ctrl->created[k], sh.created[k]);
+    }
+    __threadfence();
+    const uint32_t ticket = atomicAdd(&P.ctrl->blocks_done, 1u);
+    if (ticket == gridDim.x - 1) {
+      __threadfence();
+      volatile Ctrl* c = P.ctrl;
+      uint32_t nn[3];
+      for (int k = 0; k < 3; ++k) {
+        uint32_t n = c->count[p ^ 1][k];
+        if (n > P.cap) n = P.cap;
+        nn[k] = n;
+        c->count[p ^ 1][k] = n;
+        c->count[p][k] = 0;
+      }
+      const uint32_t ln = c->log_n;
+      if (ln < P.max_log) {
+        for (int k = 0; k < 3; ++k) P.gen_log[3 * ln + k] = nn[k];
+        c->log_n = ln + 1;
+      }
+      c->generations = c->generations + 1;
+      c->blocks_done = 0;
+      __threadfence();
+      c->gen = gen + 1;
+      __threadfence();
+    }
+  }
+}
+
+int step_kernel_max_blocks_per_sm(int precision, int block) {
+  int n = 0;
+  if (precision) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<float>, block, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<double>, block, 0);
+  return n;
+}
+
+cudaError_t launch_step(const Params& P, int precision, int grid, int block, cudaStream_t st) {
+  if (precision) k_step<float><<<grid, block, 0, st>>>(P);
+  else k_step<double><<<grid, block, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+// ======================================================================== admission
+__global__ void k_admit(Params P, uint32_t slot_base, const uint32_t* keys, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const uint32_t s = slot_base + j;
+  P.evt.key[s] = keys[j];
+  P.evt.state[s] = 1u;
+  P.evt.alive[s] = 0xFFFFFFFFu;
+  P.evt.leaked[s] = 0.0;
+  P.evt.killed[s] = 0.0;
+  double* row = P.evt.edep + (size_t)s * P.geo.n_bins;
+  for (int b = 0; b < P.geo.n_bins; ++b) row[b] = 0.0;
+}
+
+cudaError_t launch_admit(const Params& P, uint32_t slot_base, const uint32_t* keys, int n, cudaStream_t st) {
+  if (n > 0) k_admit<<<(n + 127) / 128, 128, 0, st>>>(P, slot_base, keys, n);
+  return cudaGetLastError();
+}
+
+// S12: unpack primaries into the current queues (paper Sec. 4: particles entering the
+// GPU region); a primary outside the calorimeter leaks at once
+template <class R>
+__global__ void k_init_primaries(Params P, const TrackIn* recs, const uint32_t* meta, int n, uint32_t slot_base) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const TrackIn r = recs[i];
+  const uint32_t slot = slot_base + meta[2 * i];
+  const uint32_t id = meta[2 * i + 1];
+  const int sp = r.pdg == 22 ? 0 : (r.pdg == 11 ? 1 : 2);
+  const double rest = sp == 2 ? 2.0 * kMe : 0.0;
+  const int vol = locate(P.geo, r.pos[0], r.pos[1], r.pos[2], r.dir[0], r.dir[1], r.dir[2]);
+  if (vol < 0) { atomicAdd(P.evt.leaked + slot, r.E + rest); return; }
+  const int p = __ldcg(&P.ctrl->gen) & 1;
+  const uint32_t d = atomicAdd(&P.ctrl->count[p][sp], 1u);
+  if (d >= P.cap) {
+    atomicAdd(&P.ctrl->overflow, 1ull);
+    atomicAdd(P.evt.killed + slot, r.E + rest);
+    return;
+  }
+  store_track<R>(P.q[p][sp], d, r.pos[0], r.pos[1], r.pos[2], (R)r.dir[0], (R)r.dir[1], (R)r.dir[2], r.E,
+                 (unsigned long long)id, slot, 0u, (uint32_t)vol);
+}
+
+cudaError_t launch_init_primaries(const Params& P, const TrackIn* recs, const uint32_t* meta, int n, uint32_t slot_base,
+                                  int precision, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (precision) k_init_primaries<float><<<(n + 255) / 256, 256, 0, st>>>(P, recs, meta, n, slot_base);
+  else k_init_primaries<double><<<(n + 255) / 256, 256, 0, st>>>(P, recs, meta, n, slot_base);
+  return cudaGetLastError();
+}
+
+// ======================================================================== completion
+// An event is finished when no live track of it is left in the current queues: mark
+// the slots that still have tracks with the current generation, then every active slot
+// not marked is done and goes to the done list.
+__global__ void k_mark(Params P) {
+  const uint32_t gen = __ldcg(&P.ctrl->gen);
+  const int p = gen & 1;
+  const uint32_t n0 = min(__ldcg(&P.ctrl->count[p][0]), P.cap), n1 = min(__ldcg(&P.ctrl->count[p][1]), P.cap),
+                 n2 = min(__ldcg(&P.ctrl->count[p][2]), P.cap);
+  const uint32_t total = n0 + n1 + n2;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int sp = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);
+    const uint32_t j = sp == 0 ? i : (sp == 1 ? i - n0 : i - n0 - n1);
+    const uint32_t ev = P.q[p][sp].ev[j];
+    if (P.evt.alive[ev] != gen) P.evt.alive[ev] = gen;
+  }
+}
+
+__global__ void k_finish(Params P) {
+  const uint32_t gen = __ldcg(&P.ctrl->gen);
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < P.evt.max_slots; s += gridDim.x * blockDim.x) {
+    if (P.evt.state[s] == 1u && P.evt.alive[s] != gen) {
+      P.evt.state[s] = 2u;
+      const uint32_t k = atomicAdd(&P.ctrl->done_count, 1u);
+      P.evt.done_list[k] = s;
+    }
+  }
+}
+
+cudaError_t launch_finish(const Params& P, int precision, cudaStream_t st) {
+  (void)precision;
+  k_mark<<<1216, 256, 0, st>>>(P);
+  k_finish<<<(P.evt.max_slots + 255) / 256 < 1216 ? (P.evt.max_slots + 255) / 256 : 1216, 256, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+// ======================================================================== probes
+__global__ void k_probe_philox(const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const U4 r = philox(U4{ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]}, k0, k1);
+  out[4 * i] = r.a; out[4 * i + 1] = r.b; out[4 * i + 2] = r.c; out[4 * i + 3] = r.d;
+}
+
+cudaError_t launch_probe_philox(const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t st) {
+  if (n > 0) k_probe_philox<<<(n + 127) / 128, 128, 0, st>>>(ctr, n, k0, k1, out);
+  return cudaGetLastError();
+}
+
+template <class R>
+__global__ void k_probe_interp(Params P, int s, int t, int m, const double* E, int n, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int bin;
+  R tt;
+  grid_pos<R>(E[i], &bin, &tt);
+  const size_t r = (size_t)m * kNNode + bin;
+  R v;
+  if (s == 0) v = lerp_rec<R>(tab_g<R>(P.tab) + r * kNTabG, t, tt);
+  else if (s == 1) v = lerp_rec<R>(tab_e<R>(P.tab) + r * kNTabE, t, tt);
+  else v = lerp_rec<R>(tab_p<R>(P.tab) + r * kNTabP, t, tt);
+  out[i] = (double)v;
+}
+
+cudaError_t launch_probe_interp(const Params& P, int s, int t, int m, int prec, const double* E, int n, double* out,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (prec) k_probe_interp<float><<<(n + 127) / 128, 128, 0, st>>>(P, s, t, m, E, n, out);
+  else k_probe_interp<double><<<(n + 127) / 128, 128, 0, st>>>(P, s, t, m, E, n, out);
+  return cudaGetLastError();
+}
+
+template <class R>
+__global__ void k_probe_inverse_range(Params P, int s, int m, const double* Rv, int n, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = inverse_range<R>(range_nodes<R>(P.tab, s == 2) + (size_t)m * kNNode, (R)Rv[i], kNNode - 2);
+}
+
+cudaError_t launch_probe_inverse_range(const Params& P, int s, int m, int prec, const double* R, int n, double* out,
+                                       cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (prec) k_probe_inverse_range<float><<<(n + 127) / 128, 128, 0, st>>>(P, s, m, R, n, out);
+  else k_probe_inverse_range<double><<<(n + 127) / 128, 128, 0, st>>>(P, s, m, R, n, out);
+  return cudaGetLastError();
+}
+
+template <class R>
+__global__ void k_probe_distance(Params P, const double* pos, const double* dir, const int* vol, const double* T,
+                                 const int* q, int n, double* s, int* next) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const R u[3] = {(R)dir[3 * i], (R)dir[3 * i + 1], (R)dir[3 * i + 2]};
+  int nx;
+  const double d = (q[i] != 0 && P.field_T != 0.0)
+                       ? helix_distance<R>(P.geo, P.field_T, T[i], q[i], pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], u,
+                                           vol[i], &nx)
+                       : straight_distance<R>(P.geo, pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], u, vol[i], &nx);
+  s[i] = d;
+  next[i] = nx;
+}
+
+cudaError_t launch_probe_distance(const Params& P, int prec, const double* pos, const double* dir, const int* vol,
+                                  const double* T, const int* q, int n, double* s, int* next, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (prec) k_probe_distance<float><<<(n + 127) / 128, 128, 0, st>>>(P, pos, dir, vol, T, q, n, s, next);
+  else k_probe_distance<double><<<(n + 127) / 128, 128, 0, st>>>(P, pos, dir, vol, T, q, n, s, next);
+  return cudaGetLastError();
+}
+
+template <class R>
+__global__ void k_probe_sample(Params P, int which, int m, double E, uint32_t event, int n, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Stream<R> st(P.seed, event, (unsigned long long)(i + 1), 0u);
+  const R u[3] = {(R)0, (R)0, (R)1};
+  Ixn<R> r;
+  r.happened = false; r.parent_alive = false; r.n = 0; r.parent_E = 0.0;
+  r.pd[0] = r.pd[1] = r.pd[2] = (R)0;
+  const double Tc = P.tab.Tc[m], kc = P.tab.kc[m];
+  switch (which) {
+    case 0: compton<R>(st, E, u, r); break;
+    case 1: pair<R>(st, E, u, r); break;
+    case 2: moller<R>(st, E, Tc, u, r); break;
+    case 3: bhabha<R>(st, E, Tc, u, r); break;
+    case 4: brem<R>(st, E, kc, u, r); break;
+    case 5: annihilate<R>(st, E, u, r); break;
+    default: annihilate_at_rest<R>(st, r); break;
+  }
+  double* o = out + 12 * (size_t)i;
+  o[0] = r.happened ? 1.0 : 0.0;
+  o[1] = r.parent_alive ? r.parent_E : -1.0;
+  o[2] = r.pd[0]; o[3] = r.pd[1]; o[4] = r.pd[2];
+  o[5] = r.n > 0 ? r.E[0] : -1.0;
+  o[6] = r.n > 0 ? (double)r.d[0][0] : 0.0;
+  o[7] = r.n > 0 ? (double)r.d[0][1] : 0.0;
+  o[8] = r.n > 0 ? (double)r.d[0][2] : 0.0;
+  o[9] = r.n > 1 ? r.E[1] : -1.0;
+  o[10] = r.n > 1 ? (double)r.d[1][2] : 0.0;
+  o[11] = r.n > 1 ? (double)(r.d[1][0] * r.d[0][0] + r.d[1][1] * r.d[0][1] + r.d[1][2] * r.d[0][2]) : 0.0;
+}
+
+cudaError_t launch_probe_sample(const Params& P, int which, int m, int prec, double E, uint32_t event, int n,
+                                double* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (prec) k_probe_sample<float><<<(n + 127) / 128, 128, 0, st>>>(P, which, m, E, event, n, out);
+  else k_probe_sample<double><<<(n + 127) / 128, 128, 0, st>>>(P, which, m, E, event, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace adept

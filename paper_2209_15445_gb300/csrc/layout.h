@@ -1,0 +1,144 @@
+// Memory layout shared by the host runtime (api.cu) and the kernels (kernels.cu):
+// geometry and material views, physics tables, structure-of-arrays track queues,
+// event slots and the device control block. All pointers are into the caller's arena.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace adept {
+
+constexpr int kNNode = 289;   // 1 keV .. 1 TeV, 32 bins per decade
+constexpr int kMaxMat = 8;
+constexpr int kMaxVol = 1024;
+constexpr int kNTabG = 3;     // gamma: compton, pair, photo
+constexpr int kNTabE = 4;     // e-: dedx, range, ioni, brem
+constexpr int kNTabP = 5;     // e+: dedx, range, ioni, brem, annihilation
+constexpr int kMaxLogGen = 1 << 16;
+
+struct GeoView {
+  int kind;          // 0 slab, 1 tubes
+  int n_vol;
+  int n_bins;
+  double half_xy, half_z;
+  const double* bnd;     // slab: n_vol+1 planes; tubes: n_vol radii
+  const int* vol_mat;    // material index or -1 (vacuum)
+  const int* vol_bin;    // scoring bin or -1
+};
+
+// per-material constants derived on the device from (Z, A, rho, I)
+struct MatDev {
+  double Z, A, rho, I;   // I in eV
+  double n_at, n_el;     // per mm^3
+  double inv_x0;         // 1/mm
+  double cbar, x0, x1, a_d;
+  int vacuum;
+  int pad;
+};
+
+struct TableView {
+  // (value, slope) records: [mat][node][table]
+  const double2* g64; const double2* e64; const double2* p64;
+  const float2* g32; const float2* e32; const float2* p32;
+  // range nodes for the inversion: [mat][node]
+  const double* re64; const double* rp64;
+  const float* re32; const float* rp32;
+  // production thresholds per material
+  const double* Tc; const double* kc;
+};
+
+// One species' queue in structure-of-arrays form. Directions are double (plain form)
+// or float (split form) and addressed through void pointers of the chosen width.
+struct TrackSoA {
+  double *x, *y, *z;
+  void *ux, *uy, *uz;
+  double* E;
+  unsigned long long* id;
+  uint32_t* ev;    // event slot
+  uint32_t* step;  // steps taken by this track
+  uint32_t* nav;   // volume (low 16 bits) | consecutive vacuum steps (high 16 bits)
+};
+
+// Device control block: queue sizes for the two buffer parities, generation counter,
+// statistics and the done-event list of the last chunk. Written by kernels, read by
+// the host after each chunk.
+struct Ctrl {
+  uint32_t gen;               // generations run; parity gen & 1 holds the current queues
+  uint32_t count[2][3];       // queue sizes [parity][species]
+  uint32_t blocks_done;       // last-block detection in the step kernel
+  uint32_t done_count;        // events found finished by the last finish pass
+  uint32_t log_n;             // rows written to the generation log
+  uint32_t error;             // first device-detected error code (0 = none)
+  uint32_t pad[5];
+  unsigned long long steps[3];
+  unsigned long long created[3];
+  unsigned long long overflow;
+  unsigned long long generations;
+};
+
+struct EventView {
+  uint32_t* key;       // RNG key word 1 (the caller's event number) per slot
+  uint32_t* state;     // 0 free, 1 active, 2 done
+  uint32_t* alive;     // last generation at which a live track of the slot was seen
+  double* edep;        // [slot][n_bins]
+  double* leaked;      // [slot]
+  double* killed;      // [slot]
+  uint32_t* done_list; // slots found finished
+  uint32_t max_slots;
+};
+
+struct Params {
+  GeoView geo;
+  const MatDev* mat;
+  TableView tab;
+  TrackSoA q[2][3];     // [parity][species]
+  uint32_t cap;         // tracks per species per buffer
+  Ctrl* ctrl;
+  EventView evt;
+  uint32_t* gen_log;    // [max_log][3]
+  uint32_t max_log;
+  double field_T;
+  double tcut;
+  uint32_t seed, process_mask, max_steps, max_vac;
+};
+
+// device view of one submitted particle; same layout as adept_track in adept.h
+struct TrackIn {
+  int32_t pdg;
+  int32_t pad0;
+  double E;
+  double pos[3];
+  double dir[3];
+  uint32_t event;
+  uint32_t pad1;
+};
+
+// ---- kernel launchers (kernels.cu) ----
+struct BuildScratch {
+  double* vals;     // [mat][16][kNNode] raw table values
+  double* bins;     // [mat][4][kNNode] per-bin range integrals
+};
+cudaError_t launch_build_tables(const Params& P, const double* mat_in, int n_mat, double range_cut,
+                                MatDev* mat, BuildScratch s, double2* g64, double2* e64, double2* p64,
+                                float2* g32, float2* e32, float2* p32, double* re64, double* rp64,
+                                float* re32, float* rp32, double* Tc, double* kc, cudaStream_t st);
+cudaError_t launch_step(const Params& P, int precision, int grid, int block, cudaStream_t st);
+cudaError_t launch_admit(const Params& P, uint32_t slot_base, const uint32_t* keys, int n_slots,
+                         cudaStream_t st);
+// meta: per track (event index within the request, track id)
+cudaError_t launch_init_primaries(const Params& P, const TrackIn* recs, const uint32_t* meta, int n,
+                                  uint32_t slot_base, int precision, cudaStream_t st);
+cudaError_t launch_finish(const Params& P, int precision, cudaStream_t st);
+cudaError_t launch_probe_philox(const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out,
+                                cudaStream_t st);
+cudaError_t launch_probe_interp(const Params& P, int s, int t, int m, int prec, const double* E, int n,
+                                double* out, cudaStream_t st);
+cudaError_t launch_probe_inverse_range(const Params& P, int s, int m, int prec, const double* R, int n,
+                                       double* out, cudaStream_t st);
+cudaError_t launch_probe_distance(const Params& P, int prec, const double* pos, const double* dir,
+                                  const int* vol, const double* T, const int* q, int n, double* s,
+                                  int* next, cudaStream_t st);
+cudaError_t launch_probe_sample(const Params& P, int which, int m, int prec, double E, uint32_t event,
+                                int n, double* out, cudaStream_t st);
+int step_kernel_max_blocks_per_sm(int precision, int block);
+
+}  // namespace adept

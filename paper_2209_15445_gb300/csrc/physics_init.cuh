@@ -1,0 +1,153 @@
+// Double-precision closed forms used to build the physics tables on the device at
+// initialisation (the paper keeps G4HepEm's initialisation separate from its run-time
+// functions and uploads the tables to the GPU, Sec. 2.2; here the tables are built
+// directly on the GPU). The models are the textbook forms named with each function.
+#pragma once
+#include "device.cuh"
+
+namespace adept {
+namespace init {
+
+// Klein-Nishina total cross section per electron [mm^2]. Below kappa = 0.02 its Taylor
+// series is used: the closed form cancels terms of size 1/kappa^2 down to O(1) there.
+__device__ inline double sigma_kn(double k) {
+  if (k >= 0.02) {
+    const double l = log1p(2.0 * k);
+    const double a = 1.0 + 2.0 * k;
+    const double b = (1.0 + k) / (k * k) * (2.0 * (1.0 + k) / a - l / k) + l / (2.0 * k) -
+                     (1.0 + 3.0 * k) / (a * a);
+    return 2.0 * kPi * kRe * kRe * b;
+  }
+  // exact rational coefficients of the expansion in kappa (sigma / (2 pi re^2))
+  const double c[14] = {4.0 / 3.0,          -8.0 / 3.0,         104.0 / 15.0,     -266.0 / 15.0,
+                        4576.0 / 105.0,     -2176.0 / 21.0,     15136.0 / 63.0,   -24592.0 / 45.0,
+                        606208.0 / 495.0,   -447488.0 / 165.0,  2551808.0 / 429.0, -3533312.0 / 273.0,
+                        38182912.0 / 1365.0, -6311936.0 / 105.0};
+  double s = c[13];
+  for (int i = 12; i >= 0; --i) s = s * k + c[i];
+  return 2.0 * kPi * kRe * kRe * s;
+}
+
+__device__ inline void setup_material(const double* in, MatDev* m) {
+  m->Z = in[0]; m->A = in[1]; m->rho = in[2]; m->I = in[3];
+  m->vacuum = !(m->Z > 0.0);
+  if (m->vacuum) return;
+  m->n_at = kNA * m->rho / m->A * 1e-3;
+  m->n_el = m->Z * m->n_at;
+  // Tsai radiation length (PDG): Lrad = ln(184.15 Z^-1/3), L'rad = ln(1194 Z^-2/3),
+  // Coulomb correction f(Z) of Davies, Bethe and Maximon
+  const double lz = log(m->Z);
+  const double a2 = (kAlpha * m->Z) * (kAlpha * m->Z);
+  const double f = a2 * (1.0 / (1.0 + a2) + 0.20206 - 0.0369 * a2 + 0.0083 * a2 * a2 - 0.002 * a2 * a2 * a2);
+  m->inv_x0 = 4.0 * kAlpha * kRe * kRe * m->n_at *
+              (m->Z * m->Z * ((log(184.15) - lz / 3.0) - f) + m->Z * (log(1194.0) - 2.0 * lz / 3.0));
+  // Sternheimer-Peierls general density-effect parameters for condensed media
+  const double hwp = 28.816 * sqrt(m->rho * m->Z / m->A);
+  m->cbar = 2.0 * log(m->I / hwp) + 1.0;
+  if (m->I < 100.0) {
+    m->x1 = 2.0;
+    m->x0 = m->cbar < 3.681 ? 0.2 : 0.326 * m->cbar - 1.0;
+  } else {
+    m->x1 = 3.0;
+    m->x0 = m->cbar < 5.215 ? 0.2 : 0.326 * m->cbar - 1.5;
+  }
+  const double d = m->x1 - m->x0;
+  m->a_d = (m->cbar - 2.0 * log(10.0) * m->x0) / (d * d * d);
+}
+
+__device__ inline double mu_compton(const MatDev& m, double E) { return m.n_el * sigma_kn(E / kMe); }
+
+// Bethe-Heitler in complete screening over the kinematic range of the positron fraction:
+// (w/X0)(7 - 4a(1-a))/9 with a = m/E, w = 1 - 2a
+__device__ inline double mu_pair(const MatDev& m, double E) {
+  if (!(E > 2.0 * kMe)) return 0.0;
+  const double a = kMe / E;
+  return m.inv_x0 * ((E - 2.0 * kMe) / E) * (7.0 - 4.0 * a * (1.0 - a)) / 9.0;
+}
+
+// Born-approximation K-shell photoabsorption: 4 sqrt(2) alpha^4 Z^5 sigma_Th (m/E)^3.5
+__device__ inline double mu_photo(const MatDev& m, double E) {
+  const double q = kMe / E;
+  const double a2 = kAlpha * kAlpha;
+  const double z2 = m.Z * m.Z;
+  return m.n_at * 4.0 * sqrt(2.0) * (a2 * a2) * (z2 * z2 * m.Z) * (8.0 * kPi / 3.0 * kRe * kRe) *
+         (q * q * q * sqrt(q));
+}
+
+__device__ inline double density_delta(const MatDev& m, double T) {
+  const double tau = T / kMe;
+  const double x = 0.5 * log(tau * (tau + 2.0)) / log(10.0);
+  if (x < m.x0) return 0.0;
+  const double lin = 2.0 * log(10.0) * x - m.cbar;
+  if (x >= m.x1) return lin;
+  const double r = m.x1 - x;
+  return lin + m.a_d * r * r * r;
+}
+
+// Berger-Seltzer restricted collision stopping power (ICRU 37), electrons (Moller,
+// D = min(cut, T/2)) or positrons (Bhabha, D = min(cut, T)), with the density effect
+__device__ inline double dedx_col(const MatDev& m, double T, double cut, bool positron) {
+  const double tau = T / kMe, g = tau + 1.0;
+  const double b2 = tau * (tau + 2.0) / (g * g);
+  const double Im = m.I * 1e-6 / kMe;
+  double D = positron ? T : 0.5 * T;
+  D = (cut < D ? cut : D) / kMe;
+  double F;
+  if (!positron) {
+    F = -1.0 - b2 + log((tau - D) * D) + tau / (tau - D) +
+        (0.5 * D * D + (2.0 * tau + 1.0) * log1p(-D / tau)) / (g * g);
+  } else {
+    const double y = 1.0 / (g + 1.0);
+    const double D2 = D * D, D3 = D2 * D;
+    F = log(tau * D) - (b2 / tau) * (tau + 2.0 * D - 1.5 * D2 * y - (D - D3 / 3.0) * y * y -
+                                     (0.5 * D2 - tau * D3 / 3.0 + 0.25 * D3 * D) * y * y * y);
+  }
+  double br = log(2.0 * (tau + 2.0) / (Im * Im)) + F - density_delta(m, T);
+  br = br < 0.0 ? 0.0 : br;
+  return 2.0 * kPi * kRe * kRe * kMe * m.n_el / b2 * br;
+}
+
+// Tsai radiative loss to photons below min(kc, T)
+__device__ inline double dedx_rad(const MatDev& m, double T, double kc) {
+  const double k = kc < T ? kc : T;
+  const double E = T + kMe;
+  return m.inv_x0 * (4.0 / 3.0 * k - 2.0 / 3.0 * k * k / E + k * k * k / (3.0 * E * E));
+}
+
+// Moller / Bhabha delta-ray cross sections above the cut, integrated in closed form
+__device__ inline double lambda_ioni(const MatDev& m, double T, double cut, bool positron) {
+  const double tau = T / kMe, g = tau + 1.0;
+  const double b2 = tau * (tau + 2.0) / (g * g);
+  const double ec = cut / T;
+  const double pref = m.n_el * 2.0 * kPi * kRe * kRe * kMe / T;
+  if (!positron) {
+    if (!(T > 2.0 * cut)) return 0.0;
+    const double w = (T - 2.0 * cut) / T;
+    const double gg = (2.0 * g - 1.0) / (g * g);
+    return pref / b2 * ((1.0 - gg) * 0.5 * w + w / (ec * (1.0 - ec)) - gg * log1p(w / ec));
+  }
+  if (!(T > cut)) return 0.0;
+  const double v = (T - cut) / T;
+  const double y = 1.0 / (g + 1.0), y12 = 1.0 - 2.0 * y;
+  const double B1 = 2.0 - y * y, B2 = y12 * (3.0 + y * y), B4 = y12 * y12 * y12, B3 = B4 + y12 * y12;
+  return pref * (v / (b2 * ec) - B1 * log1p(v / ec) + B2 * v - 0.5 * B3 * v * (1.0 + ec) +
+                 B4 / 3.0 * v * (1.0 + ec + ec * ec));
+}
+
+// Tsai bremsstrahlung above kc
+__device__ inline double lambda_brem(const MatDev& m, double T, double kc) {
+  if (!(T > kc)) return 0.0;
+  const double E = T + kMe, d = T - kc;
+  return m.inv_x0 * (4.0 / 3.0 * log1p(d / kc) - 4.0 / 3.0 * d / E + d * (T + kc) / (2.0 * E * E));
+}
+
+// Heitler two-photon annihilation in flight, per electron times n_el
+__device__ inline double lambda_annih(const MatDev& m, double T) {
+  const double tau = T / kMe, g = tau + 1.0;
+  const double s2 = tau * (tau + 2.0), s = sqrt(s2);
+  return m.n_el * kPi * kRe * kRe / (g + 1.0) *
+         ((g * g + 4.0 * g + 1.0) / s2 * log1p(tau + s) - (g + 3.0) / s);
+}
+
+}  // namespace init
+}  // namespace adept

@@ -1,0 +1,232 @@
+"""Transport parity of the CUDA path with the FP64 oracle (C ABI end to end).
+
+* single-interaction runs: per-generation queue sizes equal the oracle's exactly;
+* showers: per-layer mean deposit within 3 combined standard errors and 1 % on every
+  layer carrying more than 1 % of the total, and per-event energy conservation to 1e-9;
+* edge cases: empty and ragged requests, primaries outside the calorimeter, bad input,
+  too small an arena, a time budget that runs out, and queue overflow.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2209_15445_gb300 import workloads as W
+
+from gpu_common import ledger, make, need_gpu
+
+pytestmark = pytest.mark.gpu
+ME = 0.51099895
+
+
+def primary_energy(p):
+    return p.E + np.where(p.pdg == -11, 2 * ME, 0.0)
+
+
+def gpu_run(tr, prim):
+    rid = tr.submit(prim)
+    tr.transport()
+    n_ev = len(np.unique(prim.event))
+    edep, meta = tr.result(rid, n_ev)
+    return edep, meta
+
+
+def gen_log(tr):
+    from paper_2209_15445_gb300 import adept as A
+    n, log = A.adept_get_generation_log(tr.h)
+    assert n >= 0
+    return log.astype(np.int64)
+
+
+def compare_generations(tr, orc, prim, mask, precision_note=""):
+    from paper_2209_15445_gb300 import adept as A
+    A.adept_reset_generation_log(tr.h)
+    gpu_run(tr, prim)
+    log = gen_log(tr)
+    ref = orc.transport(prim, process_mask=mask, max_gen=20000)["gen_hist"].astype(np.int64)
+    # the log row g holds the queues after generation g, i.e. the oracle's generation g+1
+    last = np.nonzero(ref.sum(axis=1))[0].max()
+    assert last >= 1
+    got = np.zeros_like(ref)
+    got[0] = [np.sum(prim.pdg == 22), np.sum(prim.pdg == 11), np.sum(prim.pdg == -11)]
+    k = min(len(log), len(ref) - 1)
+    got[1:k + 1] = log[:k]
+    np.testing.assert_array_equal(got[: last + 2], ref[: last + 2])
+
+
+SINGLE = [
+    ("compton", 22, 1.0, oracle.P_COMPT),
+    ("conversion", 22, 50.0, oracle.P_CONV),
+    ("photo", 22, 0.2, oracle.P_PHOTO),
+    ("e-ioni", 11, 100.0, oracle.P_EIONI),
+    ("e-brem", 11, 300.0, oracle.P_EBREM),
+    ("e+annihilation", -11, 20.0, oracle.P_ANNIH | oracle.P_PIONI),
+]
+
+
+@pytest.mark.parametrize("name,pdg,E,mask", SINGLE)
+def test_single_interaction_generation_counts_bit_exact(name, pdg, E, mask):
+    need_gpu()
+    geom = W.slab_calorimeter()
+    tr = make(geom, precision=0, process_mask=mask, graph_generations=8)
+    n = 200
+    prim = W.Primaries(np.full(n, pdg, np.int32), np.full(n, E), np.zeros((n, 3)),
+                       np.tile([0.0, 0.0, 1.0], (n, 1)), np.arange(n, dtype=np.uint32))
+    compare_generations(tr, oracle.Oracle(geom), prim, mask)
+    tr.close()
+
+
+def test_full_physics_generation_counts_bit_exact_few_events():
+    need_gpu()
+    geom = W.slab_calorimeter()
+    tr = make(geom, precision=0, graph_generations=16)
+    prim = W.mixed(6, seed=21)
+    prim.E[:] = np.minimum(prim.E, 2000.0)
+    compare_generations(tr, oracle.Oracle(geom), prim, 0)
+    tr.close()
+
+
+def layer_check(g, o, frac=0.01, rel=0.01, nsig=3.0):
+    """per-layer means within nsig combined SE and rel on layers above frac of the total"""
+    mg, mo = g.mean(0), o.mean(0)
+    sg = g.std(0, ddof=1) / math.sqrt(len(g))
+    so = o.std(0, ddof=1) / math.sqrt(len(o))
+    big = mo > frac * mo.sum()
+    d = np.abs(mg - mo)
+    bad = big & ~((d <= nsig * np.sqrt(sg**2 + so**2)) & (d <= rel * mo))
+    assert not bad.any(), list(zip(np.nonzero(bad)[0], mg[bad], mo[bad], (d / mo)[bad]))
+    return (d / np.maximum(mo, 1e-300))[big].max()
+
+
+def shower_parity(geom, prim, precision, field_T=0.0, **kw):
+    tr = make(geom, precision=precision, field_T=field_T, arena_bytes=2 << 30, **kw)
+    edep, meta = gpu_run(tr, prim)
+    assert meta.killed_MeV == 0.0
+    tr.close()
+    orc = oracle.Oracle(geom, field_T=field_T)
+    ref = orc.transport(prim)
+    E0 = primary_energy(prim)
+    # energy conservation per request (per-event leaked/killed are summed in meta)
+    assert abs(meta.deposited_MeV + meta.leaked_MeV + meta.killed_MeV - E0.sum()) <= 1e-9 * E0.sum()
+    assert np.allclose(ledger(ref["edep"], ref["leaked"], ref["killed"]), E0, rtol=1e-12)
+    return layer_check(edep, ref["edep"]), edep, ref
+
+
+def test_shower_1gev_electrons_fp64():
+    need_gpu()
+    worst, g, o = shower_parity(W.slab_calorimeter(), W.electrons(100, 1000.0), precision=0)
+    # FP64 with the same random streams: the histories are the oracle's
+    assert worst < 1e-6
+
+
+def test_shower_10gev_electrons_split_precision():
+    need_gpu()
+    worst, g, o = shower_parity(W.slab_calorimeter(), W.electrons(1000, 1e4), precision=1)
+    print("split-precision worst per-layer relative error vs FP64 oracle:", worst)
+
+
+def test_shower_mixed_field_1T():
+    need_gpu()
+    prim = W.mixed(400, seed=31)
+    prim.E[:] = np.minimum(prim.E, 2e4)
+    for prec in (0, 1):
+        shower_parity(W.slab_calorimeter(), prim, precision=prec, field_T=1.0)
+
+
+def test_shower_barrel_3p8T():
+    need_gpu()
+    prim = W.barrel_primaries(300, seed=41)
+    prim.E[:] = np.minimum(prim.E, 5e3)
+    for prec in (0, 1):
+        shower_parity(W.barrel_calorimeter(), prim, precision=prec, field_T=3.8)
+
+
+def test_empty_and_ragged_requests():
+    need_gpu()
+    tr = make(W.slab_calorimeter(), precision=1)
+    rid = tr.submit(W.electrons(0, 1.0))
+    from paper_2209_15445_gb300 import adept as A
+    assert A.adept_poll(tr.h, rid) == 1
+    edep, meta = tr.result(rid, 0)
+    assert meta.n_events == 0 and edep.size == 0
+    edep, meta = gpu_run(tr, W.electrons(1, 10.0))
+    assert edep.shape == (1, 100) and abs(meta.deposited_MeV + meta.leaked_MeV - 10.0) < 1e-9
+    # a zero-energy particle and a photon below the tracking cut just deposit
+    p = W.Primaries(np.array([11, 22], np.int32), np.array([0.0, 5e-4]), np.zeros((2, 3)),
+                    np.array([[0, 0, 1.0], [0, 0, 1.0]]), np.array([3, 3], np.uint32))
+    edep, meta = gpu_run(tr, p)
+    assert abs(meta.deposited_MeV - 5e-4) < 1e-15
+    tr.close()
+
+
+def test_primaries_outside_leak_immediately():
+    need_gpu()
+    tr = make(W.slab_calorimeter(), precision=0)
+    p = W.Primaries(np.array([22, -11], np.int32), np.array([100.0, 5.0]),
+                    np.array([[500.0, 0, 10.0], [0, 0, -5.0]]), np.array([[0, 0, 1.0], [0, 0, 1.0]]),
+                    np.array([0, 1], np.uint32))
+    edep, meta = gpu_run(tr, p)
+    assert meta.leaked_MeV == pytest.approx(100.0 + 5.0 + 2 * ME, rel=1e-15)
+    assert edep.sum() == 0.0
+    tr.close()
+
+
+def test_invalid_input_and_small_arena():
+    need_gpu()
+    from paper_2209_15445_gb300 import adept as A
+    tr = make(W.slab_calorimeter(), precision=0)
+    bad = A.tracks_array(W.electrons(2, 10.0))
+    bad["pdg"][1] = 2212
+    rc, _ = A.adept_submit(tr.h, bad)
+    assert rc == A.EINVAL and "pdg" in A.adept_last_error(tr.h)
+    bad = A.tracks_array(W.electrons(1, 10.0))
+    bad["dir"][0] = [0, 0, 2.0]
+    assert A.adept_submit(tr.h, bad)[0] == A.EINVAL
+    tr.close()
+    with pytest.raises(A.AdeptError) as e:
+        make(W.slab_calorimeter(), arena_bytes=1 << 20)
+    assert e.value.code == A.ENOMEM
+
+
+def test_timeout_then_resume():
+    need_gpu()
+    from paper_2209_15445_gb300 import adept as A
+    tr = make(W.slab_calorimeter(), precision=1, graph_generations=1)
+    prim = W.electrons(50, 5000.0)
+    rid = tr.submit(prim)
+    rc = A.adept_transport(tr.h, 1)  # 1 us: stops after the first chunk
+    assert rc in (A.ETIMEOUT, A.OK)
+    assert A.adept_poll(tr.h, rid) in (0, 1)
+    tr.transport()
+    edep, meta = tr.result(rid, 50)
+    assert abs(meta.deposited_MeV + meta.leaked_MeV - 50 * 5000.0) < 1e-9 * 50 * 5000.0
+    tr.close()
+
+
+def test_queue_overflow_is_reported():
+    need_gpu()
+    from paper_2209_15445_gb300 import adept as A
+    tr = make(W.slab_calorimeter(), precision=1, track_capacity=2048)
+    tr.submit(W.electrons(50, 1e4))
+    rc = A.adept_transport(tr.h, 0)
+    assert rc == A.ENOMEM and "capacity" in A.adept_last_error(tr.h)
+    assert tr.stats().overflow > 0
+    tr.close()
+
+
+def test_alone_equals_in_mix():
+    """Serving: a request's result does not depend on what else is in flight (its random
+    streams are keyed by its own events and track ids)."""
+    need_gpu()
+    geom = W.barrel_calorimeter()
+    tr = make(geom, precision=1, field_T=3.8, arena_bytes=1 << 30)
+    a = W.serving_batch(300, seed=5, event=1000)
+    alone, _ = gpu_run(tr, a)
+    ids = [tr.submit(W.serving_batch(500, seed=6 + k, event=2000 + k)) for k in range(3)]
+    ra = tr.submit(a)
+    ids.append(tr.submit(W.serving_batch(800, seed=9, event=3000)))
+    tr.transport()
+    mixed, _ = tr.result(ra, 1)
+    np.testing.assert_allclose(mixed, alone, rtol=1e-9, atol=1e-9)
+    tr.close()
