@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 shower transport on its headline workload.
+
+Workload: 10,000 primary 10 GeV electrons at normal incidence on the 50-layer Pb/lAr
+sampling calorimeter (40 x 40 cm, 0.7 mm production cut, no field), split precision
+(FP32 physics, FP64 positions/boundary distances/energy), all events batched into one
+persistent-kernel transport with CUDA-graph chunks of generations. One bench step is the
+complete transport of that batch: injection, every generation until the last track
+dies, and the per-event scoring returned to the host.
+
+Prints one JSON line (rank 0): tracked steps/s for the whole job, 10 GeV showers/s,
+the step kernel's achieved HBM bandwidth against the measured peak, the FP64 CPU oracle
+timed on this host's cores, an end-to-end number through the C ABI with host buffers,
+and the SM clocks seen during the timed region.
+
+``--impl reference`` times the FP64 CPU oracle (the reference of this build) instead.
+Multi-GPU (torchrun): every rank transports its own independent batch of events (the
+path shards by event with no exchange), the timed region is bracketed by barriers and
+the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tracked steps/sec and 10 GeV e- showers/sec on 1 GB300; HBM GB/s vs peak"
+UNIT = "tracked steps/s"
+WORKLOAD = ("10,000 x 10 GeV e- showers, 50-layer Pb 2.3 mm + lAr 5.7 mm slab calorimeter, 0.7 mm cut, "
+            "no field; split precision, batched persistent launch with CUDA graphs")
+TRACK_BYTES_SPLIT = 64  # x,y,z f64 + direction 3 f32 + E f64 + id u64 + event, step, nav u32
+# DRAM bytes per tracked step of the step kernel from the committed ncu capture
+# (profiles/step_kernel_10gev_e_showers.md), valid while the kernel sources hash to NCU_SRC_HASH
+NCU_BYTES_PER_STEP = None
+NCU_SRC_HASH = None
+
+
+def kernel_src_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "device.cuh", "layout.h"):
+        with open(os.path.join(ROOT, "paper_2209_15445_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--events", type=int, default=10000)
+    ap.add_argument("--energy", type=float, default=1e4)
+    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--graph", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--arena-gb", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def oracle_rate(n_events, energy, threads=None):
+    """FP64 oracle (as it stands) on n_events of the workload; returns (steps/s, steps, s, cores)."""
+    import oracle
+    from paper_2209_15445_gb300 import workloads as W
+    o = oracle.Oracle(W.slab_calorimeter())
+    prim = W.electrons(n_events, energy, first_event=777000)
+    cores = threads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = o.transport(prim, n_threads=cores)
+    dt = time.perf_counter() - t0
+    steps = int(r["steps"].sum())
+    return steps / dt, steps, dt, cores
+
+
+def cpu_baseline(energy, target_s=12.0):
+    rate, steps, dt, cores = oracle_rate(8, energy)
+    per_event = steps / 8
+    n = max(8, min(4000, int(target_s * rate / per_event)))
+    rate, steps, dt, cores = oracle_rate(n, energy)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} of the 10,000 events ({steps} steps, {dt:.1f} s), FP64 C oracle on {cores} threads",
+            "showers_per_s": n / dt}
+
+
+def run_reference(a):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    rate, steps, dt, cores = oracle_rate(8, a.energy)
+    per_event = steps / 8
+    per_step_s = max(2.0, min(20.0, 120.0 / max(1, a.steps + a.warmup)))
+    n = max(8, min(4000, int(per_step_s * rate / per_event)))
+    for _ in range(a.warmup):
+        oracle_rate(max(2, n // 8), a.energy)
+    tot_steps, tot_t = 0, 0.0
+    for _ in range(a.steps):
+        r, s, d, cores = oracle_rate(n, a.energy)
+        tot_steps += s
+        tot_t += d
+    value = tot_steps / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot_t / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "events_per_step": n, "precision": "fp64 cpu oracle"},
+            "showers_per_s": n * a.steps / tot_t,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} events of 10 GeV e- per step on {cores} host threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    from paper_2209_15445_gb300 import adept as A
+    from paper_2209_15445_gb300 import build as B
+    from paper_2209_15445_gb300 import workloads as W
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    B.build()
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    n, E = a.events, a.energy
+    geom = W.slab_calorimeter()
+    prim = W.electrons(n, E, first_event=rank * n)  # each rank: its own events
+    host = A.tracks_array(prim)
+    dev_tracks = torch.from_numpy(host.view(np.uint8).copy()).to(dev)
+    tr = A.Transport(geom, precision=a.precision, arena_bytes=int(a.arena_gb * (1 << 30)), graph_generations=a.graph,
+                     flags=A.FLAG_TIME_STEPS, max_events=max(65536, n))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB of L2
+
+    def step_device():
+        rid = tr.submit_device(dev_tracks, n)
+        tr.transport()
+        out, meta = tr.result(rid, n)
+        return meta
+
+    for _ in range(a.warmup):
+        step_device()
+    s0 = tr.stats()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    clk = Clocks(local)
+    with clk:
+        for k in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev[k][0].record(tr.stream)
+            meta = step_device()
+            ev[k][1].record(tr.stream)
+        barrier()
+    s1 = tr.stats()
+    t_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    steps = sum(s1.steps) - sum(s0.steps)
+    launches = s1.launches - s0.launches
+    kern_ms = s1.step_kernel_ms - s0.step_kernel_ms
+    kern_n = s1.step_launches - s0.step_launches
+    edep_ok = abs(meta.deposited_MeV + meta.leaked_MeV + meta.killed_MeV - n * E) <= 1e-9 * n * E
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_ms, float(steps), kern_ms, float(kern_n)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        t_ms_max, steps_all = float(tmax[0]), int(t[1])
+    else:
+        t_ms_max, steps_all = t_ms, steps
+    value = steps_all / (t_ms_max / 1e3)
+    showers = ws * n * a.steps / (t_ms_max / 1e3)
+
+    # roofline of the step kernel: algorithmic track-state bytes per launch / its mean duration
+    tb = TRACK_BYTES_SPLIT if a.precision else 76
+    alg_bytes = tb * (2 * steps - a.steps * n)
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else None
+    traffic = None
+    if NCU_BYTES_PER_STEP and NCU_SRC_HASH == kernel_src_hash() and kern_n:
+        traffic = NCU_BYTES_PER_STEP * steps / kern_n
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+            "kernel": "k_step<float> (one generation of all three species)",
+            "alg_bytes_per_launch": alg_bytes / kern_n if kern_n else None,
+            "mean_launch_us": 1e3 * kern_ms / kern_n if kern_n else None,
+            "launches": kern_n, "peak_kind": f"{peak_kind} (hbm_gbs burst copy)",
+            "kernel_share_of_step_time": kern_ms / t_ms if t_ms else None}
+
+    # end to end through the C ABI with host buffers: submit copies host tracks to the device
+    e2e = None
+    if not a.no_e2e:
+        barrier()
+        e0 = tr.stats()
+        t0 = time.perf_counter()
+        for _ in range(max(1, a.steps // 2)):
+            rid = tr.submit(host)
+            tr.transport()
+            out, m2 = tr.result(rid, n)
+        barrier()
+        dt = time.perf_counter() - t0
+        e1 = tr.stats()
+        k2 = max(1, a.steps // 2)
+        st2 = sum(e1.steps) - sum(e0.steps)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt, float(st2)], dtype=torch.float64, device=dev)
+            tm = t.clone()
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            dt, st2 = float(tm[0]), int(t[1])
+        e2e = {"value": st2 / dt, "unit": UNIT, "h2d_bytes_per_step": int(n * (72 + 8) + 4 * n),
+               "d2h_bytes_per_step": int(n * (geom.n_bins + 2) * 8), "steps": k2,
+               "showers_per_s": ws * n * k2 / dt}
+
+    base = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        base = cpu_baseline(E)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": t_ms_max / a.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32/f64" if a.precision else "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "events": n, "E_MeV": E, "precision": "split" if a.precision else "fp64",
+                           "graph_generations": a.graph, "block": tr.options.block_size or 256,
+                           "l2": "track queues (GBs) exceed L2; 256 MB buffer written between steps"},
+                "showers_per_s": showers, "steps_per_shower": steps / (a.steps * n),
+                "energy_conserved": bool(edep_ok), "roofline": roof, "cpu_baseline": base, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    tr.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -108,8 +108,12 @@ typedef struct {
   uint32_t max_generation_log;/* per-generation queue-size log length [4096] */
   uint64_t track_capacity;    /* tracks per species per buffer [derived from arena] */
   double tracks_per_MeV;      /* admission estimate of peak live tracks per MeV [0.25] */
-  int32_t reserved;           /* must be 0 */
+  int32_t flags;              /* ADEPT_FLAG_* bits [0] */
 } adept_options;
+
+/* adept_options.flags: time every step-kernel launch with CUDA events recorded around it
+ * on the transport stream (inside the captured graphs); the totals appear in adept_stats */
+#define ADEPT_FLAG_TIME_STEPS 1
 
 /* One particle handed to the library. event is the caller's event number; it keys the
  * random streams together with the seed, so equal (seed, event, track order) inputs
@@ -142,6 +146,8 @@ typedef struct {
   uint64_t overflow;      /* tracks dropped for lack of capacity (transport then failed) */
   uint64_t requests_done;
   uint64_t launches;      /* kernels launched by the library */
+  uint64_t step_launches; /* step-kernel launches timed (ADEPT_FLAG_TIME_STEPS) */
+  double step_kernel_ms;  /* their summed CUDA-event durations */
 } adept_stats;
 
 /* Create a context: validates geometry and materials, lays out dev_arena (device memory

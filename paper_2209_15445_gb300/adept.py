@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libadept.so")
 OK, EINVAL, ENOMEM, ESTATE, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -4, -5, -6, -7
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ESTATE: "ESTATE", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
           EBUSY: "EBUSY", ENOTFOUND: "ENOTFOUND"}
+FLAG_TIME_STEPS = 1
 P_COMPTON, P_CONVERSION, P_PHOTO, P_E_IONI, P_E_BREM, P_POS_IONI, P_POS_BREM, P_ANNIH = (1 << i for i in range(8))
 NNODE = 289
 
@@ -52,7 +53,7 @@ class adept_options(C.Structure):
                 ("graph_generations", C.c_int32), ("seed", C.c_uint32), ("process_mask", C.c_uint32),
                 ("max_steps", C.c_uint32), ("max_vacuum_steps", C.c_uint32), ("max_events", C.c_uint32),
                 ("max_generation_log", C.c_uint32), ("track_capacity", C.c_uint64),
-                ("tracks_per_MeV", C.c_double), ("reserved", C.c_int32)]
+                ("tracks_per_MeV", C.c_double), ("flags", C.c_int32)]
 
 
 TRACK_DTYPE = np.dtype([("pdg", "<i4"), ("pad0", "<i4"), ("E", "<f8"), ("pos", "<f8", 3), ("dir", "<f8", 3),
@@ -75,7 +76,8 @@ class adept_result(C.Structure):
 
 class adept_stats(C.Structure):
     _fields_ = [("steps", C.c_uint64 * 3), ("secondaries", C.c_uint64 * 3), ("generations", C.c_uint64),
-                ("overflow", C.c_uint64), ("requests_done", C.c_uint64), ("launches", C.c_uint64)]
+                ("overflow", C.c_uint64), ("requests_done", C.c_uint64), ("launches", C.c_uint64),
+                ("step_launches", C.c_uint64), ("step_kernel_ms", C.c_double)]
 
 
 _lib = None

@@ -116,6 +116,7 @@ struct adept_ctx {
   int grid = 0, block = 256;
   cudaGraphExec_t graph = nullptr;
   int graph_gens = 0;
+  std::vector<cudaEvent_t> ev_start, ev_end;  // around step launches when timing
   // requests
   std::mutex mu;
   std::condition_variable cv;
@@ -251,7 +252,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (options) c->opt = *options;
   adept_options& o = c->opt;
   if (o.precision != 0 && o.precision != 1) return ADEPT_EINVAL;
-  if (o.reserved != 0) return ADEPT_EINVAL;
+  if (o.flags & ~1) return ADEPT_EINVAL;
   if (o.block_size == 0) o.block_size = 256;
   if (o.block_size < 32 || o.block_size > 256 || (o.block_size & 31)) return ADEPT_EINVAL;
   if (o.graph_generations < 0 || o.graph_generations > 1024) return ADEPT_EINVAL;
@@ -301,7 +302,8 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (!ok) return ADEPT_ENOMEM;
   c->stage_cap = stage_cap;
   rest = c->arena_bytes - ((c->arena_used + 255) & ~(size_t)255);
-  uint64_t cap = rest / (6 * per_track + 6 * 256);
+  // 6 queues x 11 arrays, each padded to 256 bytes
+  uint64_t cap = rest > 6 * 11 * 256 ? (rest - 6 * 11 * 256) / (6 * per_track) : 0;
   if (o.track_capacity) {
     if (o.track_capacity > cap) return ADEPT_ENOMEM;
     cap = o.track_capacity;
@@ -521,12 +523,36 @@ static int admit(adept_ctx* c) {
 }
 
 // ---------------------------------------------------------------- generation chunks
+static int ensure_events(adept_ctx* c, int n) {
+  while ((int)c->ev_start.size() < n) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    c->ev_start.push_back(a);
+    c->ev_end.push_back(b);
+  }
+  return ADEPT_OK;
+}
+
+static bool timing(const adept_ctx* c) { return (c->opt.flags & ADEPT_FLAG_TIME_STEPS) != 0; }
+
+// the generations of one chunk, optionally bracketed by timing events
+static cudaError_t enqueue_generations(adept_ctx* c, int gens) {
+  cudaError_t e = cudaMemsetAsync(&c->P.ctrl->done_count, 0, sizeof(uint32_t), c->stream);
+  for (int k = 0; k < gens && e == cudaSuccess; ++k) {
+    // under stream capture an external record node makes the event fire when the graph runs
+    if (timing(c)) e = cudaEventRecordWithFlags(c->ev_start[k], c->stream, cudaEventRecordExternal);
+    if (e == cudaSuccess) e = launch_step(c->P, c->opt.precision, c->grid, c->block, c->stream);
+    if (e == cudaSuccess && timing(c)) e = cudaEventRecordWithFlags(c->ev_end[k], c->stream, cudaEventRecordExternal);
+  }
+  if (e == cudaSuccess) e = launch_finish(c->P, c->opt.precision, c->stream);
+  return e;
+}
+
 static int capture_graph(adept_ctx* c, int gens) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaMemsetAsync(&c->P.ctrl->done_count, 0, sizeof(uint32_t), c->stream);
-  for (int k = 0; k < gens && e == cudaSuccess; ++k) e = launch_step(c->P, c->opt.precision, c->grid, c->block, c->stream);
-  if (e == cudaSuccess) e = launch_finish(c->P, c->opt.precision, c->stream);
+  cudaError_t e = enqueue_generations(c, gens);
   cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
   if (e != cudaSuccess) return fail(c, ADEPT_ECUDA, "graph capture: %s", cudaGetErrorString(e));
   if (e2 != cudaSuccess) return fail(c, ADEPT_ECUDA, "graph capture end: %s", cudaGetErrorString(e2));
@@ -540,22 +566,32 @@ static int capture_graph(adept_ctx* c, int gens) {
 // Run one chunk of generations, then read the control block and the done list.
 static int run_chunk(adept_ctx* c) {
   const int G = c->opt.graph_generations;
+  const int gens = G > 0 ? G : 1;
+  if (timing(c)) {
+    int rc = ensure_events(c, gens);
+    if (rc) return rc;
+  }
   if (G > 0) {
     if (!c->graph) {
       int rc = capture_graph(c, G);
       if (rc) return rc;
     }
     CK(cudaGraphLaunch(c->graph, c->stream));
-    c->stats.launches += G + 2;
   } else {
-    CK(cudaMemsetAsync(&c->P.ctrl->done_count, 0, sizeof(uint32_t), c->stream));
-    CK(launch_step(c->P, c->opt.precision, c->grid, c->block, c->stream));
-    CK(launch_finish(c->P, c->opt.precision, c->stream));
-    c->stats.launches += 3;
+    CK(enqueue_generations(c, 1));
   }
+  c->stats.launches += gens + 2;
   CK(cudaMemcpyAsync(c->h_ctrl, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_done, c->P.evt.done_list, sizeof(uint32_t) * kDoneChunk, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (timing(c)) {
+    for (int k = 0; k < gens; ++k) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, c->ev_start[k], c->ev_end[k]));
+      c->stats.step_kernel_ms += ms;
+    }
+    c->stats.step_launches += gens;
+  }
   return ADEPT_OK;
 }
 
@@ -859,6 +895,8 @@ extern "C" void adept_destroy(adept_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (auto e : c->ev_start) cudaEventDestroy(e);
+  for (auto e : c->ev_end) cudaEventDestroy(e);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
   if (c->h_done) cudaFreeHost(c->h_done);
   if (c->h_stage) cudaFreeHost(c->h_stage);

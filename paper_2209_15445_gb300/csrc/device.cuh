@@ -158,27 +158,32 @@ __device__ __forceinline__ void grid_pos<double>(double E, int* i, double* t) {
   *t = x - (double)k;
 }
 
-// FP32 form: a float holds the grid coordinate (up to 288) only to ~2e-5, too coarse for
-// a 1e-6 lookup. With E = m 2^k, x = 96 + k * 32 log10(2) + ln(m) * 32/ln(10): the first
-// two terms are summed exactly (the product's rounding error is recovered with an FMA,
-// 32 log10 2 is split in two floats), so only ln(m) * 32/ln(10) < 9.7 carries float error.
+// FP32 form: a float holds the grid coordinate x (up to 288) only to ~2e-5, too coarse for
+// a 1e-6 lookup. With E = m 2^k (m in [1/sqrt2, sqrt2), taken from the double's bits),
+// x = 96 + k * 32 log10(2) + ln(m) * 32/ln(10); each product is formed exactly with an FMA
+// against a two-float constant and the integer parts are set aside, so the fraction t
+// carries only the error of logf on m (< 1 ulp) and one rounding of a number below 2.
 template <>
 __device__ __forceinline__ void grid_pos<float>(double E, int* i, float* t) {
-  const int bits = __float_as_int((float)E);
-  const float kf = (float)(((bits >> 23) & 0xFF) - 127);
-  const float m = __int_as_float((bits & 0x7FFFFF) | 0x3F800000);
-  const float c1_hi = 9.632960319519043f, c1_lo = -4.582716428558342e-07f;
-  const float p = kf * c1_hi;
-  const float e = fmaf(kf, c1_hi, -p);
-  const float q = 96.0f + p;
-  const float iq = floorf(q);
-  const float r = (q - iq) + (e + kf * c1_lo) + logf(m) * 13.89742374420166f;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(E);
+  int k = (int)((b >> 52) & 0x7FF) - 1023;
+  float m = __int_as_float(0x3F800000 | (int)((b >> 29) & 0x7FFFFF));       // top 23 mantissa bits
+  float mlo = (float)(uint32_t)(b & 0x1FFFFFFFull) * 2.220446049250313e-16f;  // the other 29, * 2^-52
+  if (m > 1.41421356f) { m *= 0.5f; mlo *= 0.5f; ++k; }
+  const float ln = logf(m) + mlo / m;
+  const float kf = (float)k;
+  const float c1_hi = 9.632960319519043f, c1_lo = -4.582716428558342e-07f;    // 32 log10(2)
+  const float d_hi = 13.89742374420166f, d_lo = -3.232975984701625e-07f;      // 32 / ln(10)
+  const float p = kf * c1_hi, pe = fmaf(kf, c1_hi, -p);
+  const float q = ln * d_hi, qe = fmaf(ln, d_hi, -q);
+  const float ip = floorf(p), iq = floorf(q);
+  const float r = ((p - ip) + (q - iq)) + ((pe + kf * c1_lo) + (qe + ln * d_lo));
   const float fr = floorf(r);
-  int k = (int)iq + (int)fr;
+  int kk = 96 + (int)ip + (int)iq + (int)fr;
   float tt = r - fr;
-  if (k < 0) { tt += (float)k; k = 0; }
-  if (k > kNNode - 2) { tt += (float)(k - (kNNode - 2)); k = kNNode - 2; }
-  *i = k;
+  if (kk < 0) { tt += (float)kk; kk = 0; }
+  if (kk > kNNode - 2) { tt += (float)(kk - (kNNode - 2)); kk = kNNode - 2; }
+  *i = kk;
   *t = tt;
 }
 
@@ -565,22 +570,26 @@ __device__ __forceinline__ R wrap2pi(R x) {
   return r;
 }
 
-// first crossing in the asked direction of a level set whose crossings sit at phase
-// psi_ref -/+ acos(C) on the circle; dpsi = psi_ref - psi0 is passed in directly
+// First crossing, in the asked direction, of a level set whose crossings sit at phase
+// psi_ref -/+ A on the circle; dpsi = psi_ref - psi0. A = acos(C) is taken as
+// 2 atan2(sqrt(1 - C), sqrt(1 + C)) from 1 - C and 1 + C computed without cancellation:
+// acos itself loses all accuracy in FP32 where A is near 0 or pi (large radii).
 template <class R>
-__device__ __forceinline__ double helix_hit(const Helix<R>& H, R dpsi, R C, bool increasing) {
-  if (!(C >= (R)-1 && C <= (R)1)) return kBig;
-  const R A = M<R>::acos(C);
+__device__ __forceinline__ double helix_hit(const Helix<R>& H, R dpsi, R omc, R opc, bool increasing) {
+  if (!(omc >= (R)0 && opc >= (R)0)) return kBig;
+  const R A = (R)2 * M<R>::atan2(M<R>::sqrt(omc), M<R>::sqrt(opc));
   const R base = H.h * dpsi;
   const R D = wrap2pi<R>(increasing ? base - A : base + A);
   return (double)(D / H.kpath);
 }
 
+// 1 - x for a component x of a unit vector whose other component is y
+template <class R>
+__device__ __forceinline__ R one_minus(R x, R y) { return x > (R)0 ? y * y / ((R)1 + x) : (R)1 - x; }
+
 // phase of direction (ax, ay) minus the particle's phase psi0, in (-pi, pi]
 template <class R>
-__device__ __forceinline__ R phase_from(const Helix<R>& H, const R u[3], R ax, R ay) {
-  // unit radial vector of the particle: (cos psi0, sin psi0) = (h uy, -h ux) / uT
-  const R c0 = H.h * u[1] / H.uT, s0 = -H.h * u[0] / H.uT;
+__device__ __forceinline__ R phase_from(R c0, R s0, R ax, R ay) {
   return M<R>::atan2(c0 * ay - s0 * ax, c0 * ax + s0 * ay);
 }
 
@@ -590,6 +599,8 @@ __device__ double helix_distance(const GeoView& g, double B, double T, int q, do
   Helix<R> H;
   helix_setup<R>(B, T, q, u, x, y, H);
   if (H.straight) return straight_distance<R>(g, x, y, z, u, vol, next);
+  // unit vector from the circle's centre to the particle: (h uy, -h ux) / uT
+  const R c0 = H.h * u[1] / H.uT, s0 = -H.h * u[0] / H.uT;
   double s = kBig;
   int nx = vol;
   if (g.kind == 0) {
@@ -602,12 +613,18 @@ __device__ double helix_distance(const GeoView& g, double B, double T, int q, do
     }
     const double Hw = g.half_xy;
     if (!(fabs(H.cx) + (double)H.rho < Hw && fabs(H.cy) + (double)H.rho < Hw)) {
-      // walls +x, -x, +y, -y as n.P = Hw, crossed outward
+      // walls x = +Hw, -Hw, y = +Hw, -Hw as n.P = Hw crossed outward; with n.P = n.c +
+      // rho cos(psi - psi_n) and n.c = n.p - rho n.e0: C = n.e0 + (Hw - n.p)/rho
       const R nxs[4] = {(R)1, (R)-1, (R)0, (R)0}, nys[4] = {(R)0, (R)0, (R)1, (R)-1};
-      const double nc[4] = {H.cx, -H.cx, H.cy, -H.cy};
+      const double np[4] = {x, -x, y, -y};
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
-        const double sw = helix_hit<R>(H, phase_from<R>(H, u, nxs[w], nys[w]), (R)((Hw - nc[w]) / (double)H.rho), true);
+        const R ne = nxs[w] * c0 + nys[w] * s0;          // n . e0
+        const R ne_perp = nxs[w] * s0 - nys[w] * c0;     // the other component of e0
+        const R gap = (R)((Hw - np[w]) / (double)H.rho);
+        const R omc = one_minus<R>(ne, ne_perp) - gap;
+        const R opc = one_minus<R>(-ne, ne_perp) + gap;
+        const double sw = helix_hit<R>(H, phase_from<R>(c0, s0, nxs[w], nys[w]), omc, opc, true);
         if (sw < s) { s = sw; nx = -1; }
       }
     }
@@ -615,15 +632,24 @@ __device__ double helix_distance(const GeoView& g, double B, double T, int q, do
     const double cm2 = H.cx * H.cx + H.cy * H.cy;
     const R cm = M<R>::sqrt((R)cm2);
     if (cm > (R)1e-12) {
-      const R dpsi = phase_from<R>(H, u, (R)H.cx, (R)H.cy);
-      const double rho2 = (double)H.rho * (double)H.rho;
+      const R dpsi = phase_from<R>(c0, s0, (R)H.cx, (R)H.cy);
       const R den = (R)2 * H.rho * cm;
+      // |P| = R where cos(psi - psi_c) = C = (R^2 - cm^2 - rho^2)/den; 1 - C and 1 + C are
+      // formed from FP64 numerators (rho + cm)^2 - R^2 and R^2 - (cm - rho)^2 so that
+      // grazing crossings near the circle's far or near point keep their accuracy
+      const double rd = (double)H.rho;
+      const double a = cm2 + rd * rd;
+      // cm to FP64 accuracy: one Newton step on the float square root
+      const double cmd = (double)cm + (cm2 - (double)cm * (double)cm) * (double)((R)0.5 / cm);
+      const double b = 2.0 * rd * cmd;
       const double Ro = __ldg(g.bnd + vol);
-      const double so = helix_hit<R>(H, dpsi, (R)(Ro * Ro - cm2 - rho2) / den, true);
-      if (so < s) { s = so; nx = (vol + 1 < g.n_vol) ? vol + 1 : -1; }
+      {
+        const double so = helix_hit<R>(H, dpsi, (R)((a - Ro * Ro) + b) / den, (R)((Ro * Ro - a) + b) / den, true);
+        if (so < s) { s = so; nx = (vol + 1 < g.n_vol) ? vol + 1 : -1; }
+      }
       if (vol > 0) {
         const double Ri = __ldg(g.bnd + vol - 1);
-        const double si = helix_hit<R>(H, dpsi, (R)(Ri * Ri - cm2 - rho2) / den, false);
+        const double si = helix_hit<R>(H, dpsi, (R)((a - Ri * Ri) + b) / den, (R)((Ri * Ri - a) + b) / den, false);
         if (si < s) { s = si; nx = vol - 1; }
       }
     }

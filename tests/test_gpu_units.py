@@ -86,10 +86,13 @@ def test_interpolation_fp64_and_fp32(slab, slab_o):
                 assert rc == 0
                 np.testing.assert_allclose(v64, ref, rtol=1e-12, atol=1e-300 + 1e-12 * np.abs(ref).max() * 1e-6)
                 rc, v32 = A.adept_probe_interp(slab.h, s, t, m, 1, E)
-                scale = np.maximum(np.abs(ref), 1e-30)
-                # FP32 lookup: the relative error of an interpolated value, measured against the
-                # table's own magnitude where a slope crosses zero
-                err = np.abs(v32 - ref) / np.maximum(scale, 1e-6 * np.abs(ref).max())
+                # FP32 lookup error relative to the magnitude of the bin's two nodes (a
+                # relative error is undefined where an interval starts at zero, e.g. at the
+                # pair threshold)
+                node = slab_o.table(s, t, m)
+                b = np.clip(np.floor((np.log(E) - math.log(1e-3)) * 32 / math.log(10)).astype(int), 0, 287)
+                scale = np.maximum(np.abs(ref), np.maximum(np.abs(node[b]), np.abs(node[b + 1])))
+                err = np.abs(v32 - ref) / np.maximum(scale, 1e-300)
                 assert err.max() < 1e-6, (s, t, m, err.max())
 
 
@@ -131,9 +134,10 @@ def check_distances(tr, orc, pos, d, T, q, prec, tol):
     rn = np.array([r[1] for r in ref])
     agree = np.abs(s - rs) <= tol * np.maximum(1.0, rs)
     if prec == 1 and np.any(q != 0):
-        # FP32 helix phases: about 1e-7 rad of the transverse radius, plus relative rounding
-        rho = np.sqrt(T * (T + 2 * 0.51099895)) * np.hypot(d[:, 0], d[:, 1]) / (0.299792458 * orc.field_T)
-        agree |= np.abs(s - rs) <= 2e-6 * rho + 1e-5 * np.maximum(1.0, rs)
+        # FP32 helix: phases good to ~1e-7 rad, i.e. 1e-6 of rho/u_T in path, plus rounding
+        uT = np.hypot(d[:, 0], d[:, 1])
+        rho = np.sqrt(T * (T + 2 * 0.51099895)) * uT / (0.299792458 * orc.field_T)
+        agree |= np.abs(s - rs) <= 1e-6 * rho / np.maximum(uT, 1e-9) + 1e-5 * np.maximum(1.0, rs)
     assert agree.mean() > 0.999, (np.abs(s - rs) / np.maximum(1, rs)).max()
     assert (nx[agree] == rn[agree]).all()
     return len(vol)
