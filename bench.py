@@ -67,6 +67,7 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--arena-gb", type=float, default=10.0)
+    ap.add_argument("--bps", type=int, default=0, help="step-kernel blocks/SM variant (0 = library default)")
     return ap.parse_args()
 
 
@@ -146,7 +147,7 @@ def oracle_rate(n_events, energy, threads=None):
 def cpu_baseline(energy, target_s=12.0):
     rate, steps, dt, cores = oracle_rate(8, energy)
     per_event = steps / 8
-    n = max(8, min(4000, int(target_s * rate / per_event)))
+    n = max(8, min(10000, int(target_s * rate / per_event)))
     rate, steps, dt, cores = oracle_rate(n, energy)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} of the 10,000 events ({steps} steps, {dt:.1f} s), FP64 C oracle on {cores} threads",
@@ -160,7 +161,7 @@ def run_reference(a):
     rate, steps, dt, cores = oracle_rate(8, a.energy)
     per_event = steps / 8
     per_step_s = max(2.0, min(20.0, 120.0 / max(1, a.steps + a.warmup)))
-    n = max(8, min(4000, int(per_step_s * rate / per_event)))
+    n = max(8, min(10000, int(per_step_s * rate / per_event)))
     for _ in range(a.warmup):
         oracle_rate(max(2, n // 8), a.energy)
     tot_steps, tot_t = 0, 0.0
@@ -208,7 +209,7 @@ def run_ours(a):
     host = A.tracks_array(prim)
     dev_tracks = torch.from_numpy(host.view(np.uint8).copy()).to(dev)
     tr = A.Transport(geom, precision=a.precision, arena_bytes=int(a.arena_gb * (1 << 30)), graph_generations=a.graph,
-                     flags=A.FLAG_TIME_STEPS, max_events=max(65536, n))
+                     flags=A.FLAG_TIME_STEPS, max_events=max(65536, n), blocks_per_sm=a.bps)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB of L2
 
     def step_device():
@@ -302,6 +303,7 @@ def run_ours(a):
                 "dtype": "f32/f64" if a.precision else "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "events": n, "E_MeV": E, "precision": "split" if a.precision else "fp64",
                            "graph_generations": a.graph, "block": tr.options.block_size or 256,
+                           "blocks_per_sm_variant": a.bps or (2 if a.precision else 1),
                            "l2": "track queues (GBs) exceed L2; 256 MB buffer written between steps"},
                 "showers_per_s": showers, "steps_per_shower": steps / (a.steps * n),
                 "energy_conserved": bool(edep_ok), "roofline": roof, "cpu_baseline": base, "e2e": e2e,

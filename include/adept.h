@@ -97,7 +97,9 @@ typedef struct {
   int32_t precision;          /* 0: plain FP64 everywhere; 1: split, FP32 physics and helix
                                  with FP64 positions, boundary distances and energy [0] */
   int32_t block_size;         /* threads per block of the step kernel [256] */
-  int32_t blocks_per_sm;      /* persistent grid = SMs x this [occupancy limit] */
+  int32_t blocks_per_sm;      /* step-kernel variant compiled for 1..4 resident 256-thread
+                                 blocks per SM (register cap 255/128/85/64); the persistent
+                                 grid is SMs x its occupancy [2 split, 1 plain FP64] */
   int32_t graph_generations;  /* generations per captured CUDA graph; 0 = launch each
                                  generation and read the queue sizes after it [32] */
   uint32_t seed;              /* Philox key word 0 [1] */

@@ -113,7 +113,7 @@ struct adept_ctx {
   char* h_stage = nullptr;
   size_t h_stage_bytes = 0;
   // launch shape
-  int grid = 0, block = 256;
+  int grid = 0, block = 256, minb = 1;
   cudaGraphExec_t graph = nullptr;
   int graph_gens = 0;
   std::vector<cudaEvent_t> ev_start, ev_end;  // around step launches when timing
@@ -341,9 +341,10 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int bps = step_kernel_max_blocks_per_sm(o.precision, o.block_size);
+    // kernel variant: register cap for this many resident 256-thread blocks per SM
+    c->minb = o.blocks_per_sm > 0 ? std::min(4, (int)o.blocks_per_sm) : (o.precision ? 2 : 1);
+    int bps = step_kernel_max_blocks_per_sm(o.precision, c->minb, o.block_size);
     if (bps < 1) bps = 1;
-    if (o.blocks_per_sm > 0) bps = std::min(bps, (int)o.blocks_per_sm);
     c->block = o.block_size;
     c->grid = sms * bps;
   }
@@ -542,7 +543,7 @@ static cudaError_t enqueue_generations(adept_ctx* c, int gens) {
   for (int k = 0; k < gens && e == cudaSuccess; ++k) {
     // under stream capture an external record node makes the event fire when the graph runs
     if (timing(c)) e = cudaEventRecordWithFlags(c->ev_start[k], c->stream, cudaEventRecordExternal);
-    if (e == cudaSuccess) e = launch_step(c->P, c->opt.precision, c->grid, c->block, c->stream);
+    if (e == cudaSuccess) e = launch_step(c->P, c->opt.precision, c->minb, c->grid, c->block, c->stream);
     if (e == cudaSuccess && timing(c)) e = cudaEventRecordWithFlags(c->ev_end[k], c->stream, cudaEventRecordExternal);
   }
   if (e == cudaSuccess) e = launch_finish(c->P, c->opt.precision, c->stream);

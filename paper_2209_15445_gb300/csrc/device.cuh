@@ -264,7 +264,8 @@ constexpr int kMaxRej = 1000;
 // Compton scattering, Klein-Nishina, sampled by Butcher-Messel composition-rejection
 template <class R>
 __device__ void compton(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
-  const R kap = (R)(E / kMe);
+  const R Er = (R)E;
+  const R kap = Er / (R)kMe;
   const R e0 = (R)1 / ((R)1 + (R)2 * kap);
   const R a1 = M<R>::log1p((R)2 * kap);
   const R a2 = (R)0.5 * ((R)1 - e0 * e0);
@@ -277,7 +278,8 @@ __device__ void compton(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
     if (r3 < g) break;
   }
   const R phi = (R)(2.0 * kPi) * st.next();
-  const double Ep = (double)eps * E;
+  const R Epr = eps * Er;
+  const double Ep = (double)Epr;
   rotate_to<R>(u[0], u[1], u[2], (R)1 - t, phi, &r.pd[0], &r.pd[1], &r.pd[2]);
   r.happened = true;
   r.parent_alive = true;
@@ -285,8 +287,7 @@ __device__ void compton(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
   r.n = 1;
   r.sp[0] = 1;
   r.E[0] = E - Ep;
-  const R Ef = (R)E, Epf = (R)Ep;
-  R px = Ef * u[0] - Epf * r.pd[0], py = Ef * u[1] - Epf * r.pd[1], pz = Ef * u[2] - Epf * r.pd[2];
+  R px = Er * u[0] - Epr * r.pd[0], py = Er * u[1] - Epr * r.pd[1], pz = Er * u[2] - Epr * r.pd[2];
   unit<R>(&px, &py, &pz);
   r.d[0][0] = px; r.d[0][1] = py; r.d[0][2] = pz;
 }
@@ -295,15 +296,16 @@ __device__ void compton(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
 template <class R>
 __device__ void pair(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
   r.happened = false;
-  if (!(E > 2.0 * kMe)) return;
-  const R a = (R)(kMe / E);
+  const R Er = (R)E;
+  if (!(Er > (R)(2.0 * kMe))) return;
+  const R a = (R)kMe / Er;
   R x = (R)0.5;
   for (int it = 0; it < kMaxRej; ++it) {
     const R r1 = st.next(), r2 = st.next();
     x = a + ((R)1 - (R)2 * a) * r1;
     if (r2 < (R)1 - (R)(4.0 / 3.0) * x * ((R)1 - x)) break;
   }
-  const double Tp = (double)x * E - kMe;
+  const double Tp = (double)(x * Er) - kMe;
   const double Tm = E - 2.0 * kMe - Tp;
   const R phi = (R)(2.0 * kPi) * st.next();
   r.happened = true;
@@ -311,10 +313,10 @@ __device__ void pair(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
   r.n = 2;
   r.sp[0] = 2;
   r.E[0] = Tp;
-  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)(kMe / (Tp + kMe))), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
+  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)kMe / ((R)Tp + (R)kMe)), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
   r.sp[1] = 1;
   r.E[1] = Tm;
-  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)(kMe / (Tm + kMe))), phi + (R)kPi, &r.d[1][0], &r.d[1][1], &r.d[1][2]);
+  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)kMe / ((R)Tm + (R)kMe)), phi + (R)kPi, &r.d[1][0], &r.d[1][1], &r.d[1][2]);
 }
 
 template <class R>
@@ -330,13 +332,14 @@ __device__ __forceinline__ void photo(double E, const R u[3], Ixn<R>& r) {
 // free-electron two-body kinematics of a delta ray of kinetic energy Td
 template <class R>
 __device__ void delta_ray(Stream<R>& st, double T, double Td, const R u[3], Ixn<R>& r) {
-  R cd = M<R>::sqrt((R)(Td * (T + 2.0 * kMe) / (T * (Td + 2.0 * kMe))));
+  const R Tr = (R)T, Tdr = (R)Td, m2 = (R)(2.0 * kMe);
+  R cd = M<R>::sqrt(Tdr * (Tr + m2) / (Tr * (Tdr + m2)));
   cd = cd > (R)1 ? (R)1 : cd;
   const R phi = (R)(2.0 * kPi) * st.next();
   R dx, dy, dz;
   rotate_to<R>(u[0], u[1], u[2], cd, phi, &dx, &dy, &dz);
-  const R p0 = M<R>::sqrt((R)(T * (T + 2.0 * kMe)));
-  const R pd = M<R>::sqrt((R)(Td * (Td + 2.0 * kMe)));
+  const R p0 = M<R>::sqrt(Tr * (Tr + m2));
+  const R pd = M<R>::sqrt(Tdr * (Tdr + m2));
   R px = p0 * u[0] - pd * dx, py = p0 * u[1] - pd * dy, pz = p0 * u[2] - pd * dz;
   unit<R>(&px, &py, &pz);
   r.happened = true;
@@ -353,10 +356,11 @@ __device__ void delta_ray(Stream<R>& st, double T, double Td, const R u[3], Ixn<
 template <class R>
 __device__ void moller(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>& r) {
   r.happened = false;
-  if (!(T > 2.0 * Tc)) return;
-  const R g = (R)(T / kMe + 1.0);
+  const R Tr = (R)T;
+  if (!(Tr > (R)2 * (R)Tc)) return;
+  const R g = Tr / (R)kMe + (R)1;
   const R gg = ((R)2 * g - (R)1) / (g * g);
-  const R ec = (R)(Tc / T), em = (R)0.5;
+  const R ec = (R)Tc / Tr, em = (R)0.5;
   const R gmax = (R)2 + (R)0.25 * ((R)1 - gg);
   R eps = ec;
   for (int it = 0; it < kMaxRej; ++it) {
@@ -366,22 +370,23 @@ __device__ void moller(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>&
     const R f = (R)1 + q * q + ((R)1 - gg) * eps * eps - gg * q;
     if (r2 * gmax < f) break;
   }
-  delta_ray<R>(st, T, (double)eps * T, u, r);
+  delta_ray<R>(st, T, (double)(eps * Tr), u, r);
 }
 
 // Bhabha: eps from 1/eps^2 on [Tc/T, 1], accepted with 1 - b2 eps (B1 - eps (B2 - eps (B3 - eps B4)))
 template <class R>
 __device__ void bhabha(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>& r) {
   r.happened = false;
-  if (!(T > Tc)) return;
-  const R tau = (R)(T / kMe);
+  const R Tr = (R)T;
+  if (!(Tr > (R)Tc)) return;
+  const R tau = Tr / (R)kMe;
   const R g = tau + (R)1;
   const R b2 = tau * (tau + (R)2) / (g * g);
   const R y = (R)1 / (g + (R)1);
   const R y12 = (R)1 - (R)2 * y;
   const R B1 = (R)2 - y * y, B2 = y12 * ((R)3 + y * y), B4 = y12 * y12 * y12;
   const R B3 = B4 + y12 * y12;
-  const R ec = (R)(Tc / T);
+  const R ec = (R)Tc / Tr;
   R eps = ec;
   for (int it = 0; it < kMaxRej; ++it) {
     const R r1 = st.next(), r2 = st.next();
@@ -389,17 +394,17 @@ __device__ void bhabha(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>&
     const R gf = (R)1 - b2 * eps * (B1 - eps * (B2 - eps * (B3 - eps * B4)));
     if (r2 < gf) break;
   }
-  delta_ray<R>(st, T, (double)eps * T, u, r);
+  delta_ray<R>(st, T, (double)(eps * Tr), u, r);
 }
 
 // Tsai bremsstrahlung: k = kc (T/kc)^r, accepted with 1 - y + 3/4 y^2; photon at angle m/E
 template <class R>
 __device__ void brem(Stream<R>& st, double T, double kc, const R u[3], Ixn<R>& r) {
   r.happened = false;
-  if (!(T > kc)) return;
-  const double E = T + kMe;
-  const R lr = M<R>::log((R)(T / kc));
-  const R kcR = (R)kc, Ef = (R)E;
+  const R Tr = (R)T, kcR = (R)kc;
+  if (!(Tr > kcR)) return;
+  const R Ef = Tr + (R)kMe;
+  const R lr = M<R>::log(Tr / kcR);
   R k = kcR;
   for (int it = 0; it < kMaxRej; ++it) {
     const R r1 = st.next(), r2 = st.next();
@@ -417,14 +422,15 @@ __device__ void brem(Stream<R>& st, double T, double kc, const R u[3], Ixn<R>& r
   r.n = 1;
   r.sp[0] = 0;
   r.E[0] = kd;
-  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)(kMe / E)), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
+  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)kMe / Ef), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
 }
 
 // Heitler annihilation in flight: eps = E1/(T+2m) from 1/eps on [eps_min, eps_max],
 // accepted with 1 - eps + (2 g eps - 1)/(eps (g+1)^2)
 template <class R>
 __device__ void annihilate(Stream<R>& st, double T, const R u[3], Ixn<R>& r) {
-  const R tau = (R)(T / kMe);
+  const R Tr = (R)T;
+  const R tau = Tr / (R)kMe;
   const R g = tau + (R)1;
   const R sq = M<R>::sqrt(tau / (tau + (R)2));
   const R emin = (R)0.5 * ((R)1 - sq), emax = (R)0.5 * ((R)1 + sq);
@@ -438,7 +444,7 @@ __device__ void annihilate(Stream<R>& st, double T, const R u[3], Ixn<R>& r) {
     if (r2 < gf) break;
   }
   const double Etot = T + 2.0 * kMe;
-  const double E1 = (double)eps * Etot;
+  const double E1 = (double)(eps * (R)Etot);
   const double E2 = Etot - E1;
   R c1 = (eps * gp1 - (R)1) / (eps * M<R>::sqrt(tau * (tau + (R)2)));
   c1 = c1 > (R)1 ? (R)1 : (c1 < (R)-1 ? (R)-1 : c1);
@@ -451,7 +457,7 @@ __device__ void annihilate(Stream<R>& st, double T, const R u[3], Ixn<R>& r) {
   rotate_to<R>(u[0], u[1], u[2], c1, phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
   r.sp[1] = 0;
   r.E[1] = E2;
-  const R pp = M<R>::sqrt((R)(T * (T + 2.0 * kMe)));
+  const R pp = M<R>::sqrt(Tr * (Tr + (R)(2.0 * kMe)));
   const R E1f = (R)E1;
   R x = pp * u[0] - E1f * r.d[0][0], y = pp * u[1] - E1f * r.d[0][1], z = pp * u[2] - E1f * r.d[0][2];
   unit<R>(&x, &y, &z);
@@ -484,24 +490,26 @@ __device__ __forceinline__ R slab_wall(R p, R u, R H) {
   return u > (R)0 ? (H - p) / u : (u < (R)0 ? (-H - p) / u : M<R>::big());
 }
 
+// Path lengths are of type R; the FP64 work is the distance to a plane (z_plane - z)
+// and the r^2 - R^2 of a cylinder, taken from the FP64 position before rounding.
 template <class R>
-__device__ double straight_distance(const GeoView& g, double x, double y, double z, const R u[3],
-                                    int vol, int* next) {
-  double s = kBig;
+__device__ R straight_distance(const GeoView& g, double x, double y, double z, const R u[3], int vol,
+                               int* next) {
+  R s = M<R>::big();
   int nx = vol;
   if (g.kind == 0) {
     if (u[2] > (R)0) {
-      s = (double)((R)(__ldg(g.bnd + vol + 1) - z) / u[2]);
+      s = (R)(__ldg(g.bnd + vol + 1) - z) / u[2];
       nx = (vol + 1 < g.n_vol) ? vol + 1 : -1;
     } else if (u[2] < (R)0) {
-      s = (double)((R)(__ldg(g.bnd + vol) - z) / u[2]);
+      s = (R)(__ldg(g.bnd + vol) - z) / u[2];
       nx = vol - 1;
     }
     const R H = (R)g.half_xy;
     const R sx = slab_wall<R>((R)x, u[0], H);
     const R sy = slab_wall<R>((R)y, u[1], H);
-    if ((double)sx < s) { s = (double)sx; nx = -1; }
-    if ((double)sy < s) { s = (double)sy; nx = -1; }
+    if (sx < s) { s = sx; nx = -1; }
+    if (sy < s) { s = sy; nx = -1; }
   } else {
     const R a = u[0] * u[0] + u[1] * u[1];
     const R b = (R)x * u[0] + (R)y * u[1];
@@ -514,7 +522,7 @@ __device__ double straight_distance(const GeoView& g, double x, double y, double
       const R sq = M<R>::sqrt(D);
       R so = (b > (R)0) ? -co / (b + sq) : (sq - b) / a;
       so = so < (R)0 ? (R)0 : so;
-      s = (double)so;
+      s = so;
       nx = (vol + 1 < g.n_vol) ? vol + 1 : -1;
       if (vol > 0 && b < (R)0) {
         const double Ri = __ldg(g.bnd + vol - 1);
@@ -523,17 +531,17 @@ __device__ double straight_distance(const GeoView& g, double x, double y, double
         if (Di > (R)0) {
           R si = ci / (M<R>::sqrt(Di) - b);
           si = si < (R)0 ? (R)0 : si;
-          if ((double)si < s) { s = (double)si; nx = vol - 1; }
+          if (si < s) { s = si; nx = vol - 1; }
         }
       }
     }
-    double sz = kBig;
-    if (u[2] > (R)0) sz = (double)((R)(g.half_z - z) / u[2]);
-    else if (u[2] < (R)0) sz = (double)((R)(-g.half_z - z) / u[2]);
+    R sz = M<R>::big();
+    if (u[2] > (R)0) sz = (R)(g.half_z - z) / u[2];
+    else if (u[2] < (R)0) sz = (R)(-g.half_z - z) / u[2];
     if (sz < s) { s = sz; nx = -1; }
   }
   *next = nx;
-  return s < 0.0 ? 0.0 : s;
+  return s < (R)0 ? (R)0 : s;
 }
 
 // Helix in B along z: h = -sign(qB) turns the transverse direction, rho = p_T/(K |B|),
@@ -551,7 +559,8 @@ __device__ __forceinline__ void helix_setup(double B, double T, int q, const R u
   if (B == 0.0 || q == 0) return;
   const R uT = M<R>::sqrt(u[0] * u[0] + u[1] * u[1]);
   if (!(uT > (R)1e-12)) return;
-  const R pm = M<R>::sqrt((R)(T * (T + 2.0 * kMe)));
+  const R Tr = (R)T;
+  const R pm = M<R>::sqrt(Tr * (Tr + (R)(2.0 * kMe)));
   H.straight = false;
   H.uT = uT;
   H.rho = pm * uT / (R)(kHelixK * fabs(B));
@@ -575,12 +584,12 @@ __device__ __forceinline__ R wrap2pi(R x) {
 // 2 atan2(sqrt(1 - C), sqrt(1 + C)) from 1 - C and 1 + C computed without cancellation:
 // acos itself loses all accuracy in FP32 where A is near 0 or pi (large radii).
 template <class R>
-__device__ __forceinline__ double helix_hit(const Helix<R>& H, R dpsi, R omc, R opc, bool increasing) {
-  if (!(omc >= (R)0 && opc >= (R)0)) return kBig;
+__device__ __forceinline__ R helix_hit(const Helix<R>& H, R dpsi, R omc, R opc, bool increasing) {
+  if (!(omc >= (R)0 && opc >= (R)0)) return M<R>::big();
   const R A = (R)2 * M<R>::atan2(M<R>::sqrt(omc), M<R>::sqrt(opc));
   const R base = H.h * dpsi;
   const R D = wrap2pi<R>(increasing ? base - A : base + A);
-  return (double)(D / H.kpath);
+  return D / H.kpath;
 }
 
 // 1 - x for a component x of a unit vector whose other component is y
@@ -594,21 +603,21 @@ __device__ __forceinline__ R phase_from(R c0, R s0, R ax, R ay) {
 }
 
 template <class R>
-__device__ double helix_distance(const GeoView& g, double B, double T, int q, double x, double y,
+__device__ R helix_distance(const GeoView& g, double B, double T, int q, double x, double y,
                                  double z, const R u[3], int vol, int* next) {
   Helix<R> H;
   helix_setup<R>(B, T, q, u, x, y, H);
   if (H.straight) return straight_distance<R>(g, x, y, z, u, vol, next);
   // unit vector from the circle's centre to the particle: (h uy, -h ux) / uT
   const R c0 = H.h * u[1] / H.uT, s0 = -H.h * u[0] / H.uT;
-  double s = kBig;
+  R s = M<R>::big();
   int nx = vol;
   if (g.kind == 0) {
     if (u[2] > (R)0) {
-      s = (double)((R)(__ldg(g.bnd + vol + 1) - z) / u[2]);
+      s = (R)(__ldg(g.bnd + vol + 1) - z) / u[2];
       nx = (vol + 1 < g.n_vol) ? vol + 1 : -1;
     } else if (u[2] < (R)0) {
-      s = (double)((R)(__ldg(g.bnd + vol) - z) / u[2]);
+      s = (R)(__ldg(g.bnd + vol) - z) / u[2];
       nx = vol - 1;
     }
     const double Hw = g.half_xy;
@@ -624,7 +633,7 @@ __device__ double helix_distance(const GeoView& g, double B, double T, int q, do
         const R gap = (R)((Hw - np[w]) / (double)H.rho);
         const R omc = one_minus<R>(ne, ne_perp) - gap;
         const R opc = one_minus<R>(-ne, ne_perp) + gap;
-        const double sw = helix_hit<R>(H, phase_from<R>(c0, s0, nxs[w], nys[w]), omc, opc, true);
+        const R sw = helix_hit<R>(H, phase_from<R>(c0, s0, nxs[w], nys[w]), omc, opc, true);
         if (sw < s) { s = sw; nx = -1; }
       }
     }
@@ -644,20 +653,20 @@ __device__ double helix_distance(const GeoView& g, double B, double T, int q, do
       const double b = 2.0 * rd * cmd;
       const double Ro = __ldg(g.bnd + vol);
       {
-        const double so = helix_hit<R>(H, dpsi, (R)((a - Ro * Ro) + b) / den, (R)((Ro * Ro - a) + b) / den, true);
+        const R so = helix_hit<R>(H, dpsi, (R)((a - Ro * Ro) + b) / den, (R)((Ro * Ro - a) + b) / den, true);
         if (so < s) { s = so; nx = (vol + 1 < g.n_vol) ? vol + 1 : -1; }
       }
       if (vol > 0) {
         const double Ri = __ldg(g.bnd + vol - 1);
-        const double si = helix_hit<R>(H, dpsi, (R)((a - Ri * Ri) + b) / den, (R)((Ri * Ri - a) + b) / den, false);
+        const R si = helix_hit<R>(H, dpsi, (R)((a - Ri * Ri) + b) / den, (R)((Ri * Ri - a) + b) / den, false);
         if (si < s) { s = si; nx = vol - 1; }
       }
     }
-    double sz = kBig;
-    if (u[2] > (R)0) sz = (double)((R)(g.half_z - z) / u[2]);
-    else if (u[2] < (R)0) sz = (double)((R)(-g.half_z - z) / u[2]);
+    R sz = M<R>::big();
+    if (u[2] > (R)0) sz = (R)(g.half_z - z) / u[2];
+    else if (u[2] < (R)0) sz = (R)(-g.half_z - z) / u[2];
     if (sz < s) { s = sz; nx = -1; }
-    if (s >= kBig) { s = (double)((R)(2.0 * kPi) / H.kpath); nx = vol; }  // closed circle: one turn
+    if (s >= M<R>::big()) { s = (R)(2.0 * kPi) / H.kpath; nx = vol; }  // closed circle: one turn
   }
   *next = nx;
   return s;
@@ -665,15 +674,15 @@ __device__ double helix_distance(const GeoView& g, double B, double T, int q, do
 
 // move along the helix (or straight) by s; position stays double, direction in R
 template <class R>
-__device__ __forceinline__ void helix_move(double B, double T, int q, double s, double* x, double* y,
+__device__ __forceinline__ void helix_move(double B, double T, int q, R s, double* x, double* y,
                                            double* z, R u[3]) {
   Helix<R> H;
   helix_setup<R>(B, T, q, u, *x, *y, H);
   if (H.straight) {
-    *x += s * (double)u[0]; *y += s * (double)u[1]; *z += s * (double)u[2];
+    *x += (double)(s * u[0]); *y += (double)(s * u[1]); *z += (double)(s * u[2]);
     return;
   }
-  const R D = (R)s * H.kpath;
+  const R D = s * H.kpath;
   R sd, cd;
   M<R>::sincos(D, &sd, &cd);
   const R sh = M<R>::sin((R)0.5 * D);
@@ -681,7 +690,7 @@ __device__ __forceinline__ void helix_move(double B, double T, int q, double s, 
   const R a = u[0] / H.uT, b = u[1] / H.uT;
   *x += (double)(H.rho * (a * sd + H.h * b * cm1));
   *y += (double)(H.rho * (b * sd - H.h * a * cm1));
-  *z += s * (double)u[2];
+  *z += (double)(s * u[2]);
   const R u0 = u[0] * cd - H.h * u[1] * sd;
   const R u1 = u[1] * cd + H.h * u[0] * sd;
   u[0] = u0; u[1] = u1;

@@ -251,6 +251,7 @@ __device__ __forceinline__ bool on(uint32_t mask, uint32_t bit) { return mask ==
 // track advances by one step per generation. On return: alive = the track goes to the
 // next queue of its species with state t; sec holds up to two secondaries (sp < 0 for
 // one deposited below the tracking cut); dep is the energy to score in bin dep_bin.
+// Physics runs in R; positions, boundary distances and energies keep FP64 where it counts.
 template <class R, int S>
 __device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& alive, Ixn<R>& sec, double& dep,
                                            int& dep_bin, uint32_t& pstep) {
@@ -272,8 +273,10 @@ __device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& ali
   } else {
     vac = 0;
   }
+  const R tcut = (R)P.tcut;
+  const R Er = (R)t.E;
   Stream<R> rs(P.seed, __ldg(P.evt.key + t.ev), t.id, step);
-  if (t.E < P.tcut) {
+  if (Er < tcut) {
     dep = t.E;
     if (S == 2) annihilate_at_rest<R>(rs, sec);
     return;
@@ -310,34 +313,36 @@ __device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& ali
   sg2 = sg2 < (R)0 ? (R)0 : sg2;
   const R stot = sg0 + sg1 + sg2;
   // S3/S4: sampled interaction length and the range-based step limit
-  double s_phys = stot > (R)0 ? (double)(-M<R>::log(u0) / stot) : kBig;
+  R s_phys = stot > (R)0 ? -M<R>::log(u0) / stot : M<R>::big();
   if (q != 0 && m >= 0) {
     const R smax = (Rr <= (R)kRhoF) ? Rr : ((R)kAlphaR * Rr > (R)kRhoF ? (R)kAlphaR * Rr : (R)kRhoF);
-    if ((double)smax < s_phys) s_phys = (double)smax;
+    if (smax < s_phys) s_phys = smax;
   }
   // S5/S6: distance to the boundary along the straight line or helix
   int next;
   const bool field = (q != 0) && (P.field_T != 0.0);
-  const double s_geom = field ? helix_distance<R>(P.geo, P.field_T, t.E, q, t.x, t.y, t.z, t.u, vol, &next)
-                              : straight_distance<R>(P.geo, t.x, t.y, t.z, t.u, vol, &next);
+  const R s_geom = field ? helix_distance<R>(P.geo, P.field_T, t.E, q, t.x, t.y, t.z, t.u, vol, &next)
+                         : straight_distance<R>(P.geo, t.x, t.y, t.z, t.u, vol, &next);
   const bool boundary = s_geom <= s_phys;
-  const double s = boundary ? s_geom : s_phys;
+  const R s = boundary ? s_geom : s_phys;
   if (field) {
     helix_move<R>(P.field_T, t.E, q, s, &t.x, &t.y, &t.z, t.u);
   } else {
-    t.x += s * (double)t.u[0]; t.y += s * (double)t.u[1]; t.z += s * (double)t.u[2];
+    t.x += (double)(s * t.u[0]);
+    t.y += (double)(s * t.u[1]);
+    t.z += (double)(s * t.u[2]);
   }
   if (boundary && P.geo.kind == 0 && next >= 0) t.z = __ldg(P.geo.bnd + (t.u[2] > (R)0 ? vol + 1 : vol));
   t.step = step + 1;
 
   // S7: continuous loss by inverting the range table
   if (q != 0 && m >= 0) {
-    double Ep = 0.0;
-    if ((R)s < Rr) Ep = inverse_range<R>(range_nodes<R>(P.tab, S == 2) + (size_t)m * kNNode, Rr - (R)s, bin + 1);
-    if (Ep > t.E) Ep = t.E;
+    R Epr = 0;
+    if (s < Rr) Epr = inverse_range<R>(range_nodes<R>(P.tab, S == 2) + (size_t)m * kNNode, Rr - s, bin + 1);
+    const double Ep = (Epr > Er) ? t.E : (double)Epr;
     dep += t.E - Ep;
     t.E = Ep;
-    if (t.E < P.tcut) {
+    if (Epr < tcut) {
       dep += t.E;
       t.E = 0.0;
       if (S == 2) annihilate_at_rest<R>(rs, sec);
@@ -374,29 +379,25 @@ __device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& ali
   if (!sec.happened) { sec.n = 0; alive = true; return; }
   // secondaries other than positrons below the tracking cut deposit locally
   for (int k = 0; k < sec.n; ++k)
-    if (sec.sp[k] != 2 && sec.E[k] < P.tcut) { dep += sec.E[k]; sec.sp[k] = -1; }
+    if (sec.sp[k] != 2 && (R)sec.E[k] < tcut) { dep += sec.E[k]; sec.sp[k] = -1; }
   if (!sec.parent_alive) return;
   t.E = sec.parent_E;
   t.u[0] = sec.pd[0]; t.u[1] = sec.pd[1]; t.u[2] = sec.pd[2];
-  if (S == 0 && t.E < P.tcut) { dep += t.E; return; }
+  if (S == 0 && (R)t.E < tcut) { dep += t.E; return; }
   alive = true;
 }
 
-constexpr int kMaxWarps = 32;
-
-struct StepShared {
-  uint32_t n[3];
-  uint32_t wc[kMaxWarps][3];
-  uint32_t woff[kMaxWarps][3];
-  uint32_t base[3];
-  unsigned long long steps[3], created[3];
-};
-
+// One warp advances up to 32 consecutive tracks of species S and appends the results
+// (the surviving track and its secondaries) to the next queues with one atomic per
+// species per warp (S9/S11: warp-aggregated secondary allocation).
 template <class R, int S>
-__device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, StepShared& sh) {
-  const uint32_t i = base + threadIdx.x;
-  const bool active = i < sh.n[S];
+__device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, uint32_t n,
+                                         unsigned long long* nsteps, unsigned long long* ncreated) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t i = base + lane;
+  const bool active = i < n;
   Trk<R> t;
+  t.nav = 0; t.ev = 0; t.id = 0; t.E = 0.0;
   bool alive = false;
   Ixn<R> sec;
   sec.n = 0;
@@ -409,39 +410,28 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
     // S10: score the step's deposit in (event, layer, material)
     if (dep != 0.0 && dep_bin >= 0) atomicAdd(P.evt.edep + (size_t)t.ev * P.geo.n_bins + dep_bin, dep);
   }
-  // S9/S11: warp-aggregated, then block-aggregated appends to the next queues
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const bool f1 = active && sec.n > 0 && sec.sp[0] >= 0;
   const bool f2 = active && sec.n > 1 && sec.sp[1] >= 0;
   const int s1 = f1 ? sec.sp[0] : -1, s2 = f2 ? sec.sp[1] : -1;
-  uint32_t b0[3], b1[3], b2[3];
+  uint32_t b0[3], b1[3], b2[3], wbase[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     b0[k] = __ballot_sync(0xFFFFFFFFu, alive && k == S);
     b1[k] = __ballot_sync(0xFFFFFFFFu, s1 == k);
     b2[k] = __ballot_sync(0xFFFFFFFFu, s2 == k);
+    const uint32_t cnt = __popc(b0[k]) + __popc(b1[k]) + __popc(b2[k]);
+    uint32_t bk = 0;
+    if (lane == 0 && cnt) bk = atomicAdd(&P.ctrl->count[p ^ 1][k], cnt);
+    wbase[k] = __shfl_sync(0xFFFFFFFFu, bk, 0);
   }
   const uint32_t act = __ballot_sync(0xFFFFFFFFu, active);
-  if (lane == 0) {
+  nsteps[S] += __popc(act);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) sh.wc[warp][k] = __popc(b0[k]) + __popc(b1[k]) + __popc(b2[k]);
-    atomicAdd(&sh.steps[S], (unsigned long long)__popc(act));
-#pragma unroll
-    for (int k = 0; k < 3; ++k) atomicAdd(&sh.created[k], (unsigned long long)(__popc(b1[k]) + __popc(b2[k])));
-  }
-  __syncthreads();
-  const int nw = (blockDim.x + 31) >> 5;
-  if (threadIdx.x < 3) {
-    const int k = threadIdx.x;
-    uint32_t acc = 0;
-    for (int w = 0; w < nw; ++w) { sh.woff[w][k] = acc; acc += sh.wc[w][k]; }
-    sh.base[k] = acc ? atomicAdd(&P.ctrl->count[p ^ 1][k], acc) : 0u;
-  }
-  __syncthreads();
+  for (int k = 0; k < 3; ++k) ncreated[k] += __popc(b1[k]) + __popc(b2[k]);
   const TrackSoA* nq = P.q[p ^ 1];
   if (alive) {
-    const uint32_t d = sh.base[S] + sh.woff[warp][S] + __popc(b0[S] & lt);
+    const uint32_t d = wbase[S] + __popc(b0[S] & lt);
     if (d < P.cap) {
       store_track<R>(nq[S], d, t.x, t.y, t.z, t.u[0], t.u[1], t.u[2], t.E, t.id, t.ev, t.step, t.nav);
     } else {
@@ -456,7 +446,7 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
     if (sk < 0) continue;
     const uint32_t before = __popc(b0[sk]) + (k == 1 ? __popc(b1[sk]) : 0u);
     const uint32_t mine = __popc((k == 0 ? b1[sk] : b2[sk]) & lt);
-    const uint32_t d = sh.base[sk] + sh.woff[warp][sk] + before + mine;
+    const uint32_t d = wbase[sk] + before + mine;
     if (d < P.cap) {
       const unsigned long long cid = child_id(P.seed, __ldg(P.evt.key + t.ev), t.id, pstep, (uint32_t)k);
       store_track<R>(nq[sk], d, t.x, t.y, t.z, sec.d[k][0], sec.d[k][1], sec.d[k][2], sec.E[k], cid, t.ev, 0u,
@@ -466,38 +456,41 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
       atomicAdd(P.evt.killed + t.ev, sec.E[k] + (sk == 2 ? 2.0 * kMe : 0.0));
     }
   }
-  __syncthreads();
 }
 
 // One generation for all three species (paper Sec. 3: the three per-species transport
-// kernels; here one persistent launch whose blocks take tiles of the e-, e+ and gamma
-// queues). The last block to finish publishes the next queue sizes and advances gen.
-template <class R>
-__global__ void __launch_bounds__(256) k_step(Params P) {
-  __shared__ StepShared sh;
+// kernels; here one persistent launch whose warps take 32-track tiles of the e-, e+ and
+// gamma queues). The last block to finish publishes the next queue sizes and advances gen.
+template <class R, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_step(Params P) {
+  __shared__ unsigned long long s_steps[3], s_created[3];
   const uint32_t gen = __ldcg(&P.ctrl->gen);
   const int p = gen & 1;
-  if (threadIdx.x < 3) {
-    // injection may have counted past the capacity (those tracks were dropped)
-    const uint32_t n = __ldcg(&P.ctrl->count[p][threadIdx.x]);
-    sh.n[threadIdx.x] = n < P.cap ? n : P.cap;
-    sh.steps[threadIdx.x] = 0;
-    sh.created[threadIdx.x] = 0;
-  }
+  if (threadIdx.x < 3) { s_steps[threadIdx.x] = 0; s_created[threadIdx.x] = 0; }
   __syncthreads();
-  const uint32_t B = blockDim.x;
-  const uint32_t te = (sh.n[1] + B - 1) / B, tp = (sh.n[2] + B - 1) / B, tg = (sh.n[0] + B - 1) / B;
+  // injection may have counted past the capacity (those tracks were dropped)
+  const uint32_t n0 = min(__ldcg(&P.ctrl->count[p][0]), P.cap), n1 = min(__ldcg(&P.ctrl->count[p][1]), P.cap),
+                 n2 = min(__ldcg(&P.ctrl->count[p][2]), P.cap);
+  const uint32_t te = (n1 + 31) >> 5, tp = (n2 + 31) >> 5, tg = (n0 + 31) >> 5;
   const uint32_t total = te + tp + tg;
-  for (uint32_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
-    if (tile < te) run_tile<R, 1>(P, p, tile * B, sh);
-    else if (tile < te + tp) run_tile<R, 2>(P, p, (tile - te) * B, sh);
-    else run_tile<R, 0>(P, p, (tile - te - tp) * B, sh);
+  const uint32_t wpb = blockDim.x >> 5;
+  unsigned long long nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
+  for (uint32_t tile = blockIdx.x * wpb + (threadIdx.x >> 5); tile < total; tile += gridDim.x * wpb) {
+    if (tile < te) run_tile<R, 1>(P, p, tile << 5, n1, nsteps, ncreated);
+    else if (tile < te + tp) run_tile<R, 2>(P, p, (tile - te) << 5, n2, nsteps, ncreated);
+    else run_tile<R, 0>(P, p, (tile - te - tp) << 5, n0, nsteps, ncreated);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    for (int k = 0; k < 3; ++k) {
+      if (nsteps[k]) atomicAdd(&s_steps[k], nsteps[k]);
+      if (ncreated[k]) atomicAdd(&s_created[k], ncreated[k]);
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int k = 0; k < 3; ++k) {
-      if (sh.steps[k]) atomicAdd(&P.ctrl->steps[k], sh.steps[k]);
-      if (sh.created[k]) atomicAdd(&P.ctrl->created[k], sh.created[k]);
+      if (s_steps[k]) atomicAdd(&P.ctrl->steps[k], s_steps[k]);
+      if (s_created[k]) atomicAdd(&P.ctrl->created[k], s_created[k]);
     }
     __threadfence();
     const uint32_t ticket = atomicAdd(&P.ctrl->blocks_done, 1u);
@@ -526,17 +519,27 @@ __global__ void __launch_bounds__(256) k_step(Params P) {
   }
 }
 
-int step_kernel_max_blocks_per_sm(int precision, int block) {
+// The step kernel is compiled for 1..4 resident blocks of 256 threads per SM (register
+// caps 255, 128, 85, 64); the choice trades occupancy against spills and is tunable.
+template <class R>
+static const void* step_fn(int minb) {
+  switch (minb) {
+    case 1: return (const void*)k_step<R, 1>;
+    case 2: return (const void*)k_step<R, 2>;
+    case 3: return (const void*)k_step<R, 3>;
+    default: return (const void*)k_step<R, 4>;
+  }
+}
+
+int step_kernel_max_blocks_per_sm(int precision, int minb, int block) {
   int n = 0;
-  if (precision) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<float>, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<double>, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? step_fn<float>(minb) : step_fn<double>(minb), block, 0);
   return n;
 }
 
-cudaError_t launch_step(const Params& P, int precision, int grid, int block, cudaStream_t st) {
-  if (precision) k_step<float><<<grid, block, 0, st>>>(P);
-  else k_step<double><<<grid, block, 0, st>>>(P);
-  return cudaGetLastError();
+cudaError_t launch_step(const Params& P, int precision, int minb, int grid, int block, cudaStream_t st) {
+  void* args[] = {const_cast<Params*>(&P)};
+  return cudaLaunchKernel(precision ? step_fn<float>(minb) : step_fn<double>(minb), dim3(grid), dim3(block), args, 0, st);
 }
 
 // ======================================================================== admission
