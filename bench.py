@@ -67,7 +67,8 @@ def args_parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--arena-gb", type=float, default=10.0)
-    ap.add_argument("--bps", type=int, default=0, help="step-kernel blocks/SM variant (0 = library default)")
+    ap.add_argument("--bps", type=int, default=0, help="transport-kernel blocks/SM variant (0 = library default)")
+    ap.add_argument("--bps-species", type=str, default="", help="per-species variants gamma,e-,e+")
     return ap.parse_args()
 
 
@@ -209,7 +210,9 @@ def run_ours(a):
     host = A.tracks_array(prim)
     dev_tracks = torch.from_numpy(host.view(np.uint8).copy()).to(dev)
     tr = A.Transport(geom, precision=a.precision, arena_bytes=int(a.arena_gb * (1 << 30)), graph_generations=a.graph,
-                     flags=A.FLAG_TIME_STEPS, max_events=max(65536, n), blocks_per_sm=a.bps)
+                     flags=A.FLAG_TIME_STEPS, max_events=max(65536, n), blocks_per_sm=a.bps,
+                     blocks_per_sm_species=(A.C.c_int32 * 3)(*([int(x) for x in a.bps_species.split(",")]
+                                                                if a.bps_species else [0, 0, 0])))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB of L2
 
     def step_device():
@@ -238,6 +241,7 @@ def run_ours(a):
     launches = s1.launches - s0.launches
     kern_ms = s1.step_kernel_ms - s0.step_kernel_ms
     kern_n = s1.step_launches - s0.step_launches
+    species_ms = [s1.species_ms[k] - s0.species_ms[k] for k in range(3)]
     edep_ok = abs(meta.deposited_MeV + meta.leaked_MeV + meta.killed_MeV - n * E) <= 1e-9 * n * E
     if ws > 1:
         import torch.distributed as dist
@@ -261,11 +265,12 @@ def run_ours(a):
         traffic = NCU_BYTES_PER_STEP * steps / kern_n
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "kernel": "k_step<float> (one generation of all three species)",
+            "kernel": "k_transport<float, species> x3 (one generation: e-, e+, gamma)",
             "alg_bytes_per_launch": alg_bytes / kern_n if kern_n else None,
             "mean_launch_us": 1e3 * kern_ms / kern_n if kern_n else None,
             "launches": kern_n, "peak_kind": f"{peak_kind} (hbm_gbs burst copy)",
-            "kernel_share_of_step_time": kern_ms / t_ms if t_ms else None}
+            "kernel_share_of_step_time": kern_ms / t_ms if t_ms else None,
+            "species_ms_per_step": [round(x / a.steps, 3) for x in species_ms]}
 
     # end to end through the C ABI with host buffers: submit copies host tracks to the device
     e2e = None

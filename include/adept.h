@@ -97,9 +97,9 @@ typedef struct {
   int32_t precision;          /* 0: plain FP64 everywhere; 1: split, FP32 physics and helix
                                  with FP64 positions, boundary distances and energy [0] */
   int32_t block_size;         /* threads per block of the step kernel [256] */
-  int32_t blocks_per_sm;      /* step-kernel variant compiled for 1..4 resident 256-thread
-                                 blocks per SM (register cap 255/128/85/64); the persistent
-                                 grid is SMs x its occupancy [2 split, 1 plain FP64] */
+  int32_t blocks_per_sm;      /* transport-kernel variant compiled for 1..4 resident
+                                 256-thread blocks per SM (register cap 255/128/85/64); the
+                                 persistent grid is SMs x its occupancy [4 split, 1 FP64] */
   int32_t graph_generations;  /* generations per captured CUDA graph; 0 = launch each
                                  generation and read the queue sizes after it [32] */
   uint32_t seed;              /* Philox key word 0 [1] */
@@ -111,6 +111,7 @@ typedef struct {
   uint64_t track_capacity;    /* tracks per species per buffer [derived from arena] */
   double tracks_per_MeV;      /* admission estimate of peak live tracks per MeV [0.25] */
   int32_t flags;              /* ADEPT_FLAG_* bits [0] */
+  int32_t blocks_per_sm_species[3]; /* per-species override of blocks_per_sm (gamma, e-, e+) [0] */
 } adept_options;
 
 /* adept_options.flags: time every step-kernel launch with CUDA events recorded around it
@@ -148,8 +149,9 @@ typedef struct {
   uint64_t overflow;      /* tracks dropped for lack of capacity (transport then failed) */
   uint64_t requests_done;
   uint64_t launches;      /* kernels launched by the library */
-  uint64_t step_launches; /* step-kernel launches timed (ADEPT_FLAG_TIME_STEPS) */
-  double step_kernel_ms;  /* their summed CUDA-event durations */
+  uint64_t step_launches; /* generations timed (ADEPT_FLAG_TIME_STEPS) */
+  double step_kernel_ms;  /* summed CUDA-event durations of their three transport kernels */
+  double species_ms[3];   /* the same split by species kernel (gamma, e-, e+) */
 } adept_stats;
 
 /* Create a context: validates geometry and materials, lays out dev_arena (device memory

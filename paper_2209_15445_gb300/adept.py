@@ -53,7 +53,8 @@ class adept_options(C.Structure):
                 ("graph_generations", C.c_int32), ("seed", C.c_uint32), ("process_mask", C.c_uint32),
                 ("max_steps", C.c_uint32), ("max_vacuum_steps", C.c_uint32), ("max_events", C.c_uint32),
                 ("max_generation_log", C.c_uint32), ("track_capacity", C.c_uint64),
-                ("tracks_per_MeV", C.c_double), ("flags", C.c_int32)]
+                ("tracks_per_MeV", C.c_double), ("flags", C.c_int32),
+                ("blocks_per_sm_species", C.c_int32 * 3)]
 
 
 TRACK_DTYPE = np.dtype([("pdg", "<i4"), ("pad0", "<i4"), ("E", "<f8"), ("pos", "<f8", 3), ("dir", "<f8", 3),
@@ -77,7 +78,7 @@ class adept_result(C.Structure):
 class adept_stats(C.Structure):
     _fields_ = [("steps", C.c_uint64 * 3), ("secondaries", C.c_uint64 * 3), ("generations", C.c_uint64),
                 ("overflow", C.c_uint64), ("requests_done", C.c_uint64), ("launches", C.c_uint64),
-                ("step_launches", C.c_uint64), ("step_kernel_ms", C.c_double)]
+                ("step_launches", C.c_uint64), ("step_kernel_ms", C.c_double), ("species_ms", C.c_double * 3)]
 
 
 _lib = None

@@ -113,10 +113,10 @@ struct adept_ctx {
   char* h_stage = nullptr;
   size_t h_stage_bytes = 0;
   // launch shape
-  int grid = 0, block = 256, minb = 1;
+  int grid[3] = {0, 0, 0}, block = 256, minb[3] = {1, 1, 1};  // per species
   cudaGraphExec_t graph = nullptr;
   int graph_gens = 0;
-  std::vector<cudaEvent_t> ev_start, ev_end;  // around step launches when timing
+  std::vector<cudaEvent_t> ev;  // 4 per generation when timing: start, after e-, after e+, after gamma
   // requests
   std::mutex mu;
   std::condition_variable cv;
@@ -341,12 +341,15 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // kernel variant: register cap for this many resident 256-thread blocks per SM
-    c->minb = o.blocks_per_sm > 0 ? std::min(4, (int)o.blocks_per_sm) : (o.precision ? 2 : 1);
-    int bps = step_kernel_max_blocks_per_sm(o.precision, c->minb, o.block_size);
-    if (bps < 1) bps = 1;
+    // kernel variant per species: register cap for this many resident 256-thread blocks per SM
     c->block = o.block_size;
-    c->grid = sms * bps;
+    for (int sp = 0; sp < 3; ++sp) {
+      int mb = o.blocks_per_sm_species[sp] > 0 ? o.blocks_per_sm_species[sp] : o.blocks_per_sm;
+      if (mb <= 0) mb = o.precision ? 4 : 1;
+      c->minb[sp] = std::min(4, mb);
+      int bps = transport_max_blocks_per_sm(o.precision, sp, c->minb[sp], o.block_size);
+      c->grid[sp] = sms * (bps < 1 ? 1 : bps);
+    }
   }
   c->slots.init(ms);
   c->slot_req.assign(ms, 0);
@@ -525,12 +528,10 @@ static int admit(adept_ctx* c) {
 
 // ---------------------------------------------------------------- generation chunks
 static int ensure_events(adept_ctx* c, int n) {
-  while ((int)c->ev_start.size() < n) {
-    cudaEvent_t a, b;
+  while ((int)c->ev.size() < 4 * n) {
+    cudaEvent_t a;
     CK(cudaEventCreate(&a));
-    CK(cudaEventCreate(&b));
-    c->ev_start.push_back(a);
-    c->ev_end.push_back(b);
+    c->ev.push_back(a);
   }
   return ADEPT_OK;
 }
@@ -542,9 +543,14 @@ static cudaError_t enqueue_generations(adept_ctx* c, int gens) {
   cudaError_t e = cudaMemsetAsync(&c->P.ctrl->done_count, 0, sizeof(uint32_t), c->stream);
   for (int k = 0; k < gens && e == cudaSuccess; ++k) {
     // under stream capture an external record node makes the event fire when the graph runs
-    if (timing(c)) e = cudaEventRecordWithFlags(c->ev_start[k], c->stream, cudaEventRecordExternal);
-    if (e == cudaSuccess) e = launch_step(c->P, c->opt.precision, c->minb, c->grid, c->block, c->stream);
-    if (e == cudaSuccess && timing(c)) e = cudaEventRecordWithFlags(c->ev_end[k], c->stream, cudaEventRecordExternal);
+    if (timing(c)) e = cudaEventRecordWithFlags(c->ev[4 * k], c->stream, cudaEventRecordExternal);
+    // e-, e+, then gamma: the gamma kernel closes the generation
+    int j = 1;
+    for (int sp : {1, 2, 0}) {
+      if (e == cudaSuccess) e = launch_transport(c->P, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, c->stream);
+      if (e == cudaSuccess && timing(c)) e = cudaEventRecordWithFlags(c->ev[4 * k + j], c->stream, cudaEventRecordExternal);
+      ++j;
+    }
   }
   if (e == cudaSuccess) e = launch_finish(c->P, c->opt.precision, c->stream);
   return e;
@@ -581,15 +587,19 @@ static int run_chunk(adept_ctx* c) {
   } else {
     CK(enqueue_generations(c, 1));
   }
-  c->stats.launches += gens + 2;
+  c->stats.launches += 3 * gens + 2;
   CK(cudaMemcpyAsync(c->h_ctrl, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_done, c->P.evt.done_list, sizeof(uint32_t) * kDoneChunk, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (timing(c)) {
+    static const int order[3] = {1, 2, 0};
     for (int k = 0; k < gens; ++k) {
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, c->ev_start[k], c->ev_end[k]));
-      c->stats.step_kernel_ms += ms;
+      for (int j = 0; j < 3; ++j) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[4 * k + j], c->ev[4 * k + j + 1]));
+        c->stats.step_kernel_ms += ms;
+        c->stats.species_ms[order[j]] += ms;
+      }
     }
     c->stats.step_launches += gens;
   }
@@ -896,8 +906,7 @@ extern "C" void adept_destroy(adept_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
-  for (auto e : c->ev_start) cudaEventDestroy(e);
-  for (auto e : c->ev_end) cudaEventDestroy(e);
+  for (auto e : c->ev) cudaEventDestroy(e);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
   if (c->h_done) cudaFreeHost(c->h_done);
   if (c->h_stage) cudaFreeHost(c->h_stage);

@@ -38,6 +38,7 @@ template <> struct M<double> {
   static __device__ __forceinline__ double cos(double x) { return ::cos(x); }
   static __device__ __forceinline__ double sin(double x) { return ::sin(x); }
   static __device__ __forceinline__ double floor(double x) { return ::floor(x); }
+  static __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
   static __host__ __device__ constexpr double big() { return 1e300; }
   static __host__ __device__ constexpr double turn_tol() { return 0.0; }
 };
@@ -53,11 +54,44 @@ template <> struct M<float> {
   static __device__ __forceinline__ float cos(float x) { return ::cosf(x); }
   static __device__ __forceinline__ float sin(float x) { return ::sinf(x); }
   static __device__ __forceinline__ float floor(float x) { return ::floorf(x); }
+  static __device__ __forceinline__ float fabs(float x) { return ::fabsf(x); }
   static __host__ __device__ constexpr float big() { return 1e30f; }
   // a helix root within this many radians below a full turn is the current point seen
   // through FP32 rounding of the phase: treat it as an immediate crossing
   static __host__ __device__ constexpr float turn_tol() { return 2e-5f; }
 };
+
+// ---------------------------------------------------------------- FP64 <-> R conversions
+// For R = float these work on the bit patterns with integer operations (double -> float
+// truncates the significand, float -> double is exact, subnormals flush to zero), which
+// keeps the conversions off GB300's narrow FP64 pipe; the values handled (positions,
+// energies, path lengths) are far inside the float range.
+template <class R> struct Cvt;
+template <> struct Cvt<double> {
+  static __device__ __forceinline__ double r(double x) { return x; }
+  static __device__ __forceinline__ double d(double x) { return x; }
+};
+template <> struct Cvt<float> {
+  static __device__ __forceinline__ float r(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32);
+    const int e = (int)((hi >> 20) & 0x7FF) - 1023 + 127;
+    const unsigned sign = hi & 0x80000000u;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+  }
+  static __device__ __forceinline__ double d(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    if (e == 0) return __longlong_as_double((long long)sign);
+    const unsigned long long de = e == 255 ? 0x7FFull : (unsigned long long)(e - 127 + 1023);
+    return __longlong_as_double((long long)(sign | (de << 52) | ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+  }
+};
+template <class R> __device__ __forceinline__ R to_r(double x) { return Cvt<R>::r(x); }
+template <class R> __device__ __forceinline__ double to_d(R x) { return Cvt<R>::d(x); }
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon et al., SC'11: ten rounds; each multiplies counter words 0 and 2 by fixed odd
@@ -200,14 +234,14 @@ __device__ __forceinline__ R lerp_rec(const typename Pair2<R>::T* rec, int j, R 
 
 // inverse of the piecewise linear-in-ln(E) range table: 0 below the first node
 template <class R>
-__device__ __forceinline__ double inverse_range(const R* nodes, R r, int hint_hi) {
-  if (!(r >= __ldg(nodes))) return 0.0;
+__device__ __forceinline__ R inverse_range(const R* nodes, R r, int hint_hi) {
+  if (!(r >= __ldg(nodes))) return (R)0;
   int lo = 0, hi = hint_hi + 1;
   if (hi > kNNode - 1) hi = kNNode - 1;
   if (r >= __ldg(nodes + hi)) {
     lo = hi;
     hi = kNNode - 1;
-    if (r >= __ldg(nodes + hi)) return 1e6;
+    if (r >= __ldg(nodes + hi)) return (R)1e6;
   }
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -215,7 +249,7 @@ __device__ __forceinline__ double inverse_range(const R* nodes, R r, int hint_hi
   }
   const R a = __ldg(nodes + lo), b = __ldg(nodes + lo + 1);
   const R t = (r - a) / (b - a);
-  return (double)M<R>::exp(Grid<R>::lnEmin() + ((R)lo + t) * Grid<R>::dlog());
+  return M<R>::exp(Grid<R>::lnEmin() + ((R)lo + t) * Grid<R>::dlog());
 }
 
 // ---------------------------------------------------------------- direction helpers
@@ -264,7 +298,7 @@ constexpr int kMaxRej = 1000;
 // Compton scattering, Klein-Nishina, sampled by Butcher-Messel composition-rejection
 template <class R>
 __device__ void compton(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
-  const R Er = (R)E;
+  const R Er = to_r<R>(E);
   const R kap = Er / (R)kMe;
   const R e0 = (R)1 / ((R)1 + (R)2 * kap);
   const R a1 = M<R>::log1p((R)2 * kap);
@@ -279,7 +313,7 @@ __device__ void compton(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
   }
   const R phi = (R)(2.0 * kPi) * st.next();
   const R Epr = eps * Er;
-  const double Ep = (double)Epr;
+  const double Ep = to_d<R>(Epr);
   rotate_to<R>(u[0], u[1], u[2], (R)1 - t, phi, &r.pd[0], &r.pd[1], &r.pd[2]);
   r.happened = true;
   r.parent_alive = true;
@@ -296,7 +330,7 @@ __device__ void compton(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
 template <class R>
 __device__ void pair(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
   r.happened = false;
-  const R Er = (R)E;
+  const R Er = to_r<R>(E);
   if (!(Er > (R)(2.0 * kMe))) return;
   const R a = (R)kMe / Er;
   R x = (R)0.5;
@@ -305,7 +339,7 @@ __device__ void pair(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
     x = a + ((R)1 - (R)2 * a) * r1;
     if (r2 < (R)1 - (R)(4.0 / 3.0) * x * ((R)1 - x)) break;
   }
-  const double Tp = (double)(x * Er) - kMe;
+  const double Tp = to_d<R>(x * Er) - kMe;
   const double Tm = E - 2.0 * kMe - Tp;
   const R phi = (R)(2.0 * kPi) * st.next();
   r.happened = true;
@@ -313,10 +347,10 @@ __device__ void pair(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
   r.n = 2;
   r.sp[0] = 2;
   r.E[0] = Tp;
-  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)kMe / ((R)Tp + (R)kMe)), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
+  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)kMe / (to_r<R>(Tp) + (R)kMe)), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
   r.sp[1] = 1;
   r.E[1] = Tm;
-  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)kMe / ((R)Tm + (R)kMe)), phi + (R)kPi, &r.d[1][0], &r.d[1][1], &r.d[1][2]);
+  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)kMe / (to_r<R>(Tm) + (R)kMe)), phi + (R)kPi, &r.d[1][0], &r.d[1][1], &r.d[1][2]);
 }
 
 template <class R>
@@ -332,7 +366,7 @@ __device__ __forceinline__ void photo(double E, const R u[3], Ixn<R>& r) {
 // free-electron two-body kinematics of a delta ray of kinetic energy Td
 template <class R>
 __device__ void delta_ray(Stream<R>& st, double T, double Td, const R u[3], Ixn<R>& r) {
-  const R Tr = (R)T, Tdr = (R)Td, m2 = (R)(2.0 * kMe);
+  const R Tr = to_r<R>(T), Tdr = to_r<R>(Td), m2 = (R)(2.0 * kMe);
   R cd = M<R>::sqrt(Tdr * (Tr + m2) / (Tr * (Tdr + m2)));
   cd = cd > (R)1 ? (R)1 : cd;
   const R phi = (R)(2.0 * kPi) * st.next();
@@ -356,11 +390,11 @@ __device__ void delta_ray(Stream<R>& st, double T, double Td, const R u[3], Ixn<
 template <class R>
 __device__ void moller(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>& r) {
   r.happened = false;
-  const R Tr = (R)T;
-  if (!(Tr > (R)2 * (R)Tc)) return;
+  const R Tr = to_r<R>(T);
+  if (!(Tr > (R)2 * to_r<R>(Tc))) return;
   const R g = Tr / (R)kMe + (R)1;
   const R gg = ((R)2 * g - (R)1) / (g * g);
-  const R ec = (R)Tc / Tr, em = (R)0.5;
+  const R ec = to_r<R>(Tc) / Tr, em = (R)0.5;
   const R gmax = (R)2 + (R)0.25 * ((R)1 - gg);
   R eps = ec;
   for (int it = 0; it < kMaxRej; ++it) {
@@ -370,15 +404,15 @@ __device__ void moller(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>&
     const R f = (R)1 + q * q + ((R)1 - gg) * eps * eps - gg * q;
     if (r2 * gmax < f) break;
   }
-  delta_ray<R>(st, T, (double)(eps * Tr), u, r);
+  delta_ray<R>(st, T, to_d<R>(eps * Tr), u, r);
 }
 
 // Bhabha: eps from 1/eps^2 on [Tc/T, 1], accepted with 1 - b2 eps (B1 - eps (B2 - eps (B3 - eps B4)))
 template <class R>
 __device__ void bhabha(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>& r) {
   r.happened = false;
-  const R Tr = (R)T;
-  if (!(Tr > (R)Tc)) return;
+  const R Tr = to_r<R>(T);
+  if (!(Tr > to_r<R>(Tc))) return;
   const R tau = Tr / (R)kMe;
   const R g = tau + (R)1;
   const R b2 = tau * (tau + (R)2) / (g * g);
@@ -386,7 +420,7 @@ __device__ void bhabha(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>&
   const R y12 = (R)1 - (R)2 * y;
   const R B1 = (R)2 - y * y, B2 = y12 * ((R)3 + y * y), B4 = y12 * y12 * y12;
   const R B3 = B4 + y12 * y12;
-  const R ec = (R)Tc / Tr;
+  const R ec = to_r<R>(Tc) / Tr;
   R eps = ec;
   for (int it = 0; it < kMaxRej; ++it) {
     const R r1 = st.next(), r2 = st.next();
@@ -394,14 +428,14 @@ __device__ void bhabha(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>&
     const R gf = (R)1 - b2 * eps * (B1 - eps * (B2 - eps * (B3 - eps * B4)));
     if (r2 < gf) break;
   }
-  delta_ray<R>(st, T, (double)(eps * Tr), u, r);
+  delta_ray<R>(st, T, to_d<R>(eps * Tr), u, r);
 }
 
 // Tsai bremsstrahlung: k = kc (T/kc)^r, accepted with 1 - y + 3/4 y^2; photon at angle m/E
 template <class R>
 __device__ void brem(Stream<R>& st, double T, double kc, const R u[3], Ixn<R>& r) {
   r.happened = false;
-  const R Tr = (R)T, kcR = (R)kc;
+  const R Tr = to_r<R>(T), kcR = to_r<R>(kc);
   if (!(Tr > kcR)) return;
   const R Ef = Tr + (R)kMe;
   const R lr = M<R>::log(Tr / kcR);
@@ -412,8 +446,7 @@ __device__ void brem(Stream<R>& st, double T, double kc, const R u[3], Ixn<R>& r
     const R y = k / Ef;
     if (r2 < (R)1 - y + (R)0.75 * y * y) break;
   }
-  double kd = (double)k;
-  if (kd > T) kd = T;  // FP32 rounding of kc (T/kc)^r can step past T
+  const double kd = (k >= Tr) ? T : to_d<R>(k);  // FP32 rounding of kc (T/kc)^r can reach T
   const R phi = (R)(2.0 * kPi) * st.next();
   r.happened = true;
   r.parent_alive = true;
@@ -429,7 +462,7 @@ __device__ void brem(Stream<R>& st, double T, double kc, const R u[3], Ixn<R>& r
 // accepted with 1 - eps + (2 g eps - 1)/(eps (g+1)^2)
 template <class R>
 __device__ void annihilate(Stream<R>& st, double T, const R u[3], Ixn<R>& r) {
-  const R Tr = (R)T;
+  const R Tr = to_r<R>(T);
   const R tau = Tr / (R)kMe;
   const R g = tau + (R)1;
   const R sq = M<R>::sqrt(tau / (tau + (R)2));
@@ -444,7 +477,7 @@ __device__ void annihilate(Stream<R>& st, double T, const R u[3], Ixn<R>& r) {
     if (r2 < gf) break;
   }
   const double Etot = T + 2.0 * kMe;
-  const double E1 = (double)(eps * (R)Etot);
+  const double E1 = to_d<R>(eps * to_r<R>(Etot));
   const double E2 = Etot - E1;
   R c1 = (eps * gp1 - (R)1) / (eps * M<R>::sqrt(tau * (tau + (R)2)));
   c1 = c1 > (R)1 ? (R)1 : (c1 < (R)-1 ? (R)-1 : c1);
@@ -499,24 +532,24 @@ __device__ R straight_distance(const GeoView& g, double x, double y, double z, c
   int nx = vol;
   if (g.kind == 0) {
     if (u[2] > (R)0) {
-      s = (R)(__ldg(g.bnd + vol + 1) - z) / u[2];
+      s = to_r<R>(__ldg(g.bnd + vol + 1) - z) / u[2];
       nx = (vol + 1 < g.n_vol) ? vol + 1 : -1;
     } else if (u[2] < (R)0) {
-      s = (R)(__ldg(g.bnd + vol) - z) / u[2];
+      s = to_r<R>(__ldg(g.bnd + vol) - z) / u[2];
       nx = vol - 1;
     }
     const R H = (R)g.half_xy;
-    const R sx = slab_wall<R>((R)x, u[0], H);
-    const R sy = slab_wall<R>((R)y, u[1], H);
+    const R sx = slab_wall<R>(to_r<R>(x), u[0], H);
+    const R sy = slab_wall<R>(to_r<R>(y), u[1], H);
     if (sx < s) { s = sx; nx = -1; }
     if (sy < s) { s = sy; nx = -1; }
   } else {
     const R a = u[0] * u[0] + u[1] * u[1];
-    const R b = (R)x * u[0] + (R)y * u[1];
+    const R b = to_r<R>(x) * u[0] + to_r<R>(y) * u[1];
     const double r2 = x * x + y * y;
     if (a > (R)0) {
       const double Ro = __ldg(g.bnd + vol);
-      const R co = (R)(r2 - Ro * Ro);
+      const R co = to_r<R>(r2 - Ro * Ro);
       R D = b * b - a * co;
       D = D < (R)0 ? (R)0 : D;
       const R sq = M<R>::sqrt(D);
@@ -526,7 +559,7 @@ __device__ R straight_distance(const GeoView& g, double x, double y, double z, c
       nx = (vol + 1 < g.n_vol) ? vol + 1 : -1;
       if (vol > 0 && b < (R)0) {
         const double Ri = __ldg(g.bnd + vol - 1);
-        const R ci = (R)(r2 - Ri * Ri);
+        const R ci = to_r<R>(r2 - Ri * Ri);
         const R Di = b * b - a * ci;
         if (Di > (R)0) {
           R si = ci / (M<R>::sqrt(Di) - b);
@@ -536,8 +569,8 @@ __device__ R straight_distance(const GeoView& g, double x, double y, double z, c
       }
     }
     R sz = M<R>::big();
-    if (u[2] > (R)0) sz = (R)(g.half_z - z) / u[2];
-    else if (u[2] < (R)0) sz = (R)(-g.half_z - z) / u[2];
+    if (u[2] > (R)0) sz = to_r<R>(g.half_z - z) / u[2];
+    else if (u[2] < (R)0) sz = to_r<R>(-g.half_z - z) / u[2];
     if (sz < s) { s = sz; nx = -1; }
   }
   *next = nx;
@@ -559,14 +592,14 @@ __device__ __forceinline__ void helix_setup(double B, double T, int q, const R u
   if (B == 0.0 || q == 0) return;
   const R uT = M<R>::sqrt(u[0] * u[0] + u[1] * u[1]);
   if (!(uT > (R)1e-12)) return;
-  const R Tr = (R)T;
+  const R Tr = to_r<R>(T);
   const R pm = M<R>::sqrt(Tr * (Tr + (R)(2.0 * kMe)));
   H.straight = false;
   H.uT = uT;
   H.rho = pm * uT / (R)(kHelixK * fabs(B));
   H.h = ((q > 0) == (B > 0.0)) ? (R)-1 : (R)1;
-  H.cx = x - (double)(H.rho * H.h * u[1] / uT);
-  H.cy = y + (double)(H.rho * H.h * u[0] / uT);
+  H.cx = x - to_d<R>(H.rho * H.h * u[1] / uT);
+  H.cy = y + to_d<R>(H.rho * H.h * u[0] / uT);
   H.kpath = uT / H.rho;
 }
 
@@ -614,14 +647,14 @@ __device__ R helix_distance(const GeoView& g, double B, double T, int q, double 
   int nx = vol;
   if (g.kind == 0) {
     if (u[2] > (R)0) {
-      s = (R)(__ldg(g.bnd + vol + 1) - z) / u[2];
+      s = to_r<R>(__ldg(g.bnd + vol + 1) - z) / u[2];
       nx = (vol + 1 < g.n_vol) ? vol + 1 : -1;
     } else if (u[2] < (R)0) {
-      s = (R)(__ldg(g.bnd + vol) - z) / u[2];
+      s = to_r<R>(__ldg(g.bnd + vol) - z) / u[2];
       nx = vol - 1;
     }
     const double Hw = g.half_xy;
-    if (!(fabs(H.cx) + (double)H.rho < Hw && fabs(H.cy) + (double)H.rho < Hw)) {
+    if (!(M<R>::fabs(to_r<R>(H.cx)) + H.rho < (R)Hw && M<R>::fabs(to_r<R>(H.cy)) + H.rho < (R)Hw)) {
       // walls x = +Hw, -Hw, y = +Hw, -Hw as n.P = Hw crossed outward; with n.P = n.c +
       // rho cos(psi - psi_n) and n.c = n.p - rho n.e0: C = n.e0 + (Hw - n.p)/rho
       const R nxs[4] = {(R)1, (R)-1, (R)0, (R)0}, nys[4] = {(R)0, (R)0, (R)1, (R)-1};
@@ -630,7 +663,7 @@ __device__ R helix_distance(const GeoView& g, double B, double T, int q, double 
       for (int w = 0; w < 4; ++w) {
         const R ne = nxs[w] * c0 + nys[w] * s0;          // n . e0
         const R ne_perp = nxs[w] * s0 - nys[w] * c0;     // the other component of e0
-        const R gap = (R)((Hw - np[w]) / (double)H.rho);
+        const R gap = to_r<R>(Hw - np[w]) / H.rho;
         const R omc = one_minus<R>(ne, ne_perp) - gap;
         const R opc = one_minus<R>(-ne, ne_perp) + gap;
         const R sw = helix_hit<R>(H, phase_from<R>(c0, s0, nxs[w], nys[w]), omc, opc, true);
@@ -639,32 +672,33 @@ __device__ R helix_distance(const GeoView& g, double B, double T, int q, double 
     }
   } else {
     const double cm2 = H.cx * H.cx + H.cy * H.cy;
-    const R cm = M<R>::sqrt((R)cm2);
+    const R cm = M<R>::sqrt(to_r<R>(cm2));
     if (cm > (R)1e-12) {
-      const R dpsi = phase_from<R>(c0, s0, (R)H.cx, (R)H.cy);
+      const R dpsi = phase_from<R>(c0, s0, to_r<R>(H.cx), to_r<R>(H.cy));
       const R den = (R)2 * H.rho * cm;
       // |P| = R where cos(psi - psi_c) = C = (R^2 - cm^2 - rho^2)/den; 1 - C and 1 + C are
       // formed from FP64 numerators (rho + cm)^2 - R^2 and R^2 - (cm - rho)^2 so that
       // grazing crossings near the circle's far or near point keep their accuracy
-      const double rd = (double)H.rho;
+      const double rd = to_d<R>(H.rho);
       const double a = cm2 + rd * rd;
       // cm to FP64 accuracy: one Newton step on the float square root
-      const double cmd = (double)cm + (cm2 - (double)cm * (double)cm) * (double)((R)0.5 / cm);
+      const double cmf = to_d<R>(cm);
+      const double cmd = cmf + (cm2 - cmf * cmf) * to_d<R>((R)0.5 / cm);
       const double b = 2.0 * rd * cmd;
       const double Ro = __ldg(g.bnd + vol);
       {
-        const R so = helix_hit<R>(H, dpsi, (R)((a - Ro * Ro) + b) / den, (R)((Ro * Ro - a) + b) / den, true);
+        const R so = helix_hit<R>(H, dpsi, to_r<R>((a - Ro * Ro) + b) / den, to_r<R>((Ro * Ro - a) + b) / den, true);
         if (so < s) { s = so; nx = (vol + 1 < g.n_vol) ? vol + 1 : -1; }
       }
       if (vol > 0) {
         const double Ri = __ldg(g.bnd + vol - 1);
-        const R si = helix_hit<R>(H, dpsi, (R)((a - Ri * Ri) + b) / den, (R)((Ri * Ri - a) + b) / den, false);
+        const R si = helix_hit<R>(H, dpsi, to_r<R>((a - Ri * Ri) + b) / den, to_r<R>((Ri * Ri - a) + b) / den, false);
         if (si < s) { s = si; nx = vol - 1; }
       }
     }
     R sz = M<R>::big();
-    if (u[2] > (R)0) sz = (R)(g.half_z - z) / u[2];
-    else if (u[2] < (R)0) sz = (R)(-g.half_z - z) / u[2];
+    if (u[2] > (R)0) sz = to_r<R>(g.half_z - z) / u[2];
+    else if (u[2] < (R)0) sz = to_r<R>(-g.half_z - z) / u[2];
     if (sz < s) { s = sz; nx = -1; }
     if (s >= M<R>::big()) { s = (R)(2.0 * kPi) / H.kpath; nx = vol; }  // closed circle: one turn
   }
@@ -679,7 +713,7 @@ __device__ __forceinline__ void helix_move(double B, double T, int q, R s, doubl
   Helix<R> H;
   helix_setup<R>(B, T, q, u, *x, *y, H);
   if (H.straight) {
-    *x += (double)(s * u[0]); *y += (double)(s * u[1]); *z += (double)(s * u[2]);
+    *x += to_d<R>(s * u[0]); *y += to_d<R>(s * u[1]); *z += to_d<R>(s * u[2]);
     return;
   }
   const R D = s * H.kpath;
@@ -688,9 +722,9 @@ __device__ __forceinline__ void helix_move(double B, double T, int q, R s, doubl
   const R sh = M<R>::sin((R)0.5 * D);
   const R cm1 = (R)-2 * sh * sh;
   const R a = u[0] / H.uT, b = u[1] / H.uT;
-  *x += (double)(H.rho * (a * sd + H.h * b * cm1));
-  *y += (double)(H.rho * (b * sd - H.h * a * cm1));
-  *z += (double)(s * u[2]);
+  *x += to_d<R>(H.rho * (a * sd + H.h * b * cm1));
+  *y += to_d<R>(H.rho * (b * sd - H.h * a * cm1));
+  *z += to_d<R>(s * u[2]);
   const R u0 = u[0] * cd - H.h * u[1] * sd;
   const R u1 = u[1] * cd + H.h * u[0] * sd;
   u[0] = u0; u[1] = u1;

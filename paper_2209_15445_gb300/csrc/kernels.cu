@@ -274,7 +274,7 @@ __device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& ali
     vac = 0;
   }
   const R tcut = (R)P.tcut;
-  const R Er = (R)t.E;
+  const R Er = to_r<R>(t.E);
   Stream<R> rs(P.seed, __ldg(P.evt.key + t.ev), t.id, step);
   if (Er < tcut) {
     dep = t.E;
@@ -328,9 +328,9 @@ __device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& ali
   if (field) {
     helix_move<R>(P.field_T, t.E, q, s, &t.x, &t.y, &t.z, t.u);
   } else {
-    t.x += (double)(s * t.u[0]);
-    t.y += (double)(s * t.u[1]);
-    t.z += (double)(s * t.u[2]);
+    t.x += to_d<R>(s * t.u[0]);
+    t.y += to_d<R>(s * t.u[1]);
+    t.z += to_d<R>(s * t.u[2]);
   }
   if (boundary && P.geo.kind == 0 && next >= 0) t.z = __ldg(P.geo.bnd + (t.u[2] > (R)0 ? vol + 1 : vol));
   t.step = step + 1;
@@ -339,7 +339,7 @@ __device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& ali
   if (q != 0 && m >= 0) {
     R Epr = 0;
     if (s < Rr) Epr = inverse_range<R>(range_nodes<R>(P.tab, S == 2) + (size_t)m * kNNode, Rr - s, bin + 1);
-    const double Ep = (Epr > Er) ? t.E : (double)Epr;
+    const double Ep = (Epr > Er) ? t.E : to_d<R>(Epr);
     dep += t.E - Ep;
     t.E = Ep;
     if (Epr < tcut) {
@@ -378,12 +378,13 @@ __device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& ali
   }
   if (!sec.happened) { sec.n = 0; alive = true; return; }
   // secondaries other than positrons below the tracking cut deposit locally
-  for (int k = 0; k < sec.n; ++k)
-    if (sec.sp[k] != 2 && (R)sec.E[k] < tcut) { dep += sec.E[k]; sec.sp[k] = -1; }
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    if (k < sec.n && sec.sp[k] != 2 && to_r<R>(sec.E[k]) < tcut) { dep += sec.E[k]; sec.sp[k] = -1; }
   if (!sec.parent_alive) return;
   t.E = sec.parent_E;
   t.u[0] = sec.pd[0]; t.u[1] = sec.pd[1]; t.u[2] = sec.pd[2];
-  if (S == 0 && (R)t.E < tcut) { dep += t.E; return; }
+  if (S == 0 && to_r<R>(t.E) < tcut) { dep += t.E; return; }
   alive = true;
 }
 
@@ -408,7 +409,7 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
     load_track<R>(P.q[p][S], i, t);
     step_track<R, S>(P, t, alive, sec, dep, dep_bin, pstep);
     // S10: score the step's deposit in (event, layer, material)
-    if (dep != 0.0 && dep_bin >= 0) atomicAdd(P.evt.edep + (size_t)t.ev * P.geo.n_bins + dep_bin, dep);
+    if (dep_bin >= 0 && __double_as_longlong(dep) != 0) atomicAdd(P.evt.edep + (size_t)t.ev * P.geo.n_bins + dep_bin, dep);
   }
   const uint32_t lt = (1u << lane) - 1u;
   const bool f1 = active && sec.n > 0 && sec.sp[0] >= 0;
@@ -430,6 +431,8 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
 #pragma unroll
   for (int k = 0; k < 3; ++k) ncreated[k] += __popc(b1[k]) + __popc(b2[k]);
   const TrackSoA* nq = P.q[p ^ 1];
+  // pick entry k of a 3-array without dynamic indexing (which would place it in local memory)
+  auto pick = [](const uint32_t* a, int k) { return k == 0 ? a[0] : (k == 1 ? a[1] : a[2]); };
   if (alive) {
     const uint32_t d = wbase[S] + __popc(b0[S] & lt);
     if (d < P.cap) {
@@ -444,9 +447,9 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
   for (int k = 0; k < 2; ++k) {
     const int sk = k == 0 ? s1 : s2;
     if (sk < 0) continue;
-    const uint32_t before = __popc(b0[sk]) + (k == 1 ? __popc(b1[sk]) : 0u);
-    const uint32_t mine = __popc((k == 0 ? b1[sk] : b2[sk]) & lt);
-    const uint32_t d = wbase[sk] + before + mine;
+    const uint32_t before = __popc(pick(b0, sk)) + (k == 1 ? __popc(pick(b1, sk)) : 0u);
+    const uint32_t mine = __popc((k == 0 ? pick(b1, sk) : pick(b2, sk)) & lt);
+    const uint32_t d = pick(wbase, sk) + before + mine;
     if (d < P.cap) {
       const unsigned long long cid = child_id(P.seed, __ldg(P.evt.key + t.ev), t.id, pstep, (uint32_t)k);
       store_track<R>(nq[sk], d, t.x, t.y, t.z, sec.d[k][0], sec.d[k][1], sec.d[k][2], sec.E[k], cid, t.ev, 0u,
@@ -458,88 +461,89 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
   }
 }
 
-// One generation for all three species (paper Sec. 3: the three per-species transport
-// kernels; here one persistent launch whose warps take 32-track tiles of the e-, e+ and
-// gamma queues). The last block to finish publishes the next queue sizes and advances gen.
-template <class R, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_step(Params P) {
-  __shared__ unsigned long long s_steps[3], s_created[3];
+// One generation of one species (paper Sec. 3: TransportElectrons, TransportPositrons and
+// TransportGammas). Persistent launch: each warp takes 32-track tiles of the current queue.
+// The three run back to back per generation (e-, e+, gamma); the last block of the gamma
+// kernel publishes the next queue sizes and advances the generation.
+template <class R, int S, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
+  __shared__ unsigned long long s_steps, s_created[3];
   const uint32_t gen = __ldcg(&P.ctrl->gen);
   const int p = gen & 1;
-  if (threadIdx.x < 3) { s_steps[threadIdx.x] = 0; s_created[threadIdx.x] = 0; }
+  if (threadIdx.x == 0) { s_steps = 0; s_created[0] = s_created[1] = s_created[2] = 0; }
   __syncthreads();
   // injection may have counted past the capacity (those tracks were dropped)
-  const uint32_t n0 = min(__ldcg(&P.ctrl->count[p][0]), P.cap), n1 = min(__ldcg(&P.ctrl->count[p][1]), P.cap),
-                 n2 = min(__ldcg(&P.ctrl->count[p][2]), P.cap);
-  const uint32_t te = (n1 + 31) >> 5, tp = (n2 + 31) >> 5, tg = (n0 + 31) >> 5;
-  const uint32_t total = te + tp + tg;
+  const uint32_t n = min(__ldcg(&P.ctrl->count[p][S]), P.cap);
+  const uint32_t tiles = (n + 31) >> 5;
   const uint32_t wpb = blockDim.x >> 5;
   unsigned long long nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
-  for (uint32_t tile = blockIdx.x * wpb + (threadIdx.x >> 5); tile < total; tile += gridDim.x * wpb) {
-    if (tile < te) run_tile<R, 1>(P, p, tile << 5, n1, nsteps, ncreated);
-    else if (tile < te + tp) run_tile<R, 2>(P, p, (tile - te) << 5, n2, nsteps, ncreated);
-    else run_tile<R, 0>(P, p, (tile - te - tp) << 5, n0, nsteps, ncreated);
-  }
+  for (uint32_t tile = blockIdx.x * wpb + (threadIdx.x >> 5); tile < tiles; tile += gridDim.x * wpb)
+    run_tile<R, S>(P, p, tile << 5, n, nsteps, ncreated);
   if ((threadIdx.x & 31) == 0) {
-    for (int k = 0; k < 3; ++k) {
-      if (nsteps[k]) atomicAdd(&s_steps[k], nsteps[k]);
+    if (nsteps[S]) atomicAdd(&s_steps, nsteps[S]);
+    for (int k = 0; k < 3; ++k)
       if (ncreated[k]) atomicAdd(&s_created[k], ncreated[k]);
-    }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < 3; ++k) {
-      if (s_steps[k]) atomicAdd(&P.ctrl->steps[k], s_steps[k]);
-      if (s_created[k]) atomicAdd(&P.ctrl->created[k], s_created[k]);
-    }
-    __threadfence();
-    const uint32_t ticket = atomicAdd(&P.ctrl->blocks_done, 1u);
-    if (ticket == gridDim.x - 1) {
-      __threadfence();
-      volatile Ctrl* c = P.ctrl;
-      uint32_t nn[3];
-      for (int k = 0; k < 3; ++k) {
-        uint32_t n = c->count[p ^ 1][k];
-        if (n > P.cap) n = P.cap;
-        nn[k] = n;
-        c->count[p ^ 1][k] = n;
-        c->count[p][k] = 0;
-      }
-      const uint32_t ln = c->log_n;
-      if (ln < P.max_log) {
-        for (int k = 0; k < 3; ++k) P.gen_log[3 * ln + k] = nn[k];
-        c->log_n = ln + 1;
-      }
-      c->generations = c->generations + 1;
-      c->blocks_done = 0;
-      __threadfence();
-      c->gen = gen + 1;
-      __threadfence();
-    }
+  if (threadIdx.x != 0) return;
+  if (s_steps) atomicAdd(&P.ctrl->steps[S], s_steps);
+  for (int k = 0; k < 3; ++k)
+    if (s_created[k]) atomicAdd(&P.ctrl->created[k], s_created[k]);
+  if (S != 0) return;
+  __threadfence();
+  const uint32_t ticket = atomicAdd(&P.ctrl->blocks_done, 1u);
+  if (ticket != gridDim.x - 1) return;
+  __threadfence();
+  volatile Ctrl* c = P.ctrl;
+  uint32_t nn[3];
+  for (int k = 0; k < 3; ++k) {
+    uint32_t m = c->count[p ^ 1][k];
+    if (m > P.cap) m = P.cap;
+    nn[k] = m;
+    c->count[p ^ 1][k] = m;
+    c->count[p][k] = 0;
   }
+  const uint32_t ln = c->log_n;
+  if (ln < P.max_log) {
+    for (int k = 0; k < 3; ++k) P.gen_log[3 * ln + k] = nn[k];
+    c->log_n = ln + 1;
+  }
+  c->generations = c->generations + 1;
+  c->blocks_done = 0;
+  __threadfence();
+  c->gen = gen + 1;
+  __threadfence();
 }
 
-// The step kernel is compiled for 1..4 resident blocks of 256 threads per SM (register
-// caps 255, 128, 85, 64); the choice trades occupancy against spills and is tunable.
-template <class R>
-static const void* step_fn(int minb) {
+// Each species kernel is compiled for 1..4 resident blocks of 256 threads per SM
+// (register caps 255, 128, 85, 64); the choice trades occupancy against spills.
+template <class R, int S>
+static const void* transport_fn(int minb) {
   switch (minb) {
-    case 1: return (const void*)k_step<R, 1>;
-    case 2: return (const void*)k_step<R, 2>;
-    case 3: return (const void*)k_step<R, 3>;
-    default: return (const void*)k_step<R, 4>;
+    case 1: return (const void*)k_transport<R, S, 1>;
+    case 2: return (const void*)k_transport<R, S, 2>;
+    case 3: return (const void*)k_transport<R, S, 3>;
+    default: return (const void*)k_transport<R, S, 4>;
   }
 }
 
-int step_kernel_max_blocks_per_sm(int precision, int minb, int block) {
+template <class R>
+static const void* transport_fn(int species, int minb) {
+  return species == 0 ? transport_fn<R, 0>(minb) : (species == 1 ? transport_fn<R, 1>(minb) : transport_fn<R, 2>(minb));
+}
+
+int transport_max_blocks_per_sm(int precision, int species, int minb, int block) {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, precision ? step_fn<float>(minb) : step_fn<double>(minb), block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &n, precision ? transport_fn<float>(species, minb) : transport_fn<double>(species, minb), block, 0);
   return n;
 }
 
-cudaError_t launch_step(const Params& P, int precision, int minb, int grid, int block, cudaStream_t st) {
+cudaError_t launch_transport(const Params& P, int precision, int species, int minb, int grid, int block,
+                             cudaStream_t st) {
   void* args[] = {const_cast<Params*>(&P)};
-  return cudaLaunchKernel(precision ? step_fn<float>(minb) : step_fn<double>(minb), dim3(grid), dim3(block), args, 0, st);
+  return cudaLaunchKernel(precision ? transport_fn<float>(species, minb) : transport_fn<double>(species, minb),
+                          dim3(grid), dim3(block), args, 0, st);
 }
 
 // ======================================================================== admission

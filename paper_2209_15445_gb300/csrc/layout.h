@@ -121,7 +121,9 @@ cudaError_t launch_build_tables(const Params& P, const double* mat_in, int n_mat
                                 MatDev* mat, BuildScratch s, double2* g64, double2* e64, double2* p64,
                                 float2* g32, float2* e32, float2* p32, double* re64, double* rp64,
                                 float* re32, float* rp32, double* Tc, double* kc, cudaStream_t st);
-cudaError_t launch_step(const Params& P, int precision, int minb, int grid, int block, cudaStream_t st);
+// one generation of one species; species 0 (gamma) must run last: it closes the generation
+cudaError_t launch_transport(const Params& P, int precision, int species, int minb, int grid, int block,
+                             cudaStream_t st);
 cudaError_t launch_admit(const Params& P, uint32_t slot_base, const uint32_t* keys, int n_slots,
                          cudaStream_t st);
 // meta: per track (event index within the request, track id)
@@ -139,6 +141,6 @@ cudaError_t launch_probe_distance(const Params& P, int prec, const double* pos, 
                                   int* next, cudaStream_t st);
 cudaError_t launch_probe_sample(const Params& P, int which, int m, int prec, double E, uint32_t event,
                                 int n, double* out, cudaStream_t st);
-int step_kernel_max_blocks_per_sm(int precision, int minb, int block);
+int transport_max_blocks_per_sm(int precision, int species, int minb, int block);
 
 }  // namespace adept
