@@ -237,6 +237,28 @@ int adept_probe_distance(adept_ctx* ctx, int32_t prec, const double* host_pos,
 int adept_probe_sample(adept_ctx* ctx, int32_t which, int32_t m, int32_t prec, double E,
                        uint32_t event, size_t n, double* host_out);
 
+/* Table build without any allocation, for callers that cannot allocate device memory:
+ * code that runs under a host framework which owns every device allocation (a fixed
+ * device budget handed out by someone else), or that must not add an allocation, with its
+ * latency and its failure mode, to its path. The paper has no counterpart.
+ * Computes, for n_materials (1..ADEPT_NOALLOC_MAX_MATERIALS) materials and a range cut, the
+ * same FP64 tables and production thresholds as adept_build_tables:
+ *   dev_tables: caller-owned device memory, [n_materials][12][289] doubles: gamma (compton,
+ *               pair, photo), e- (dedx, range, ioni, brem), e+ (dedx, range, ioni, brem,
+ *               annihilation) at the 289 grid energies (zeros for vacuum);
+ *   dev_cuts:   caller-owned device memory, [n_materials][2] doubles (e-/e+ cut, gamma cut).
+ * Needs no context and allocates nothing: its working rows (ADEPT_NOALLOC_MAX_MATERIALS x
+ * 17 x 289 doubles, 157 KB) are a static device array that every GPU loading the library
+ * holds until exit. The first call on a device looks up that array's device address with the
+ * device current; make that first call before any stream capture. Work is queued on stream
+ * (a cudaStream_t; results are ready when the stream reaches it). Every call shares the
+ * array, so calls that overlap on the GPU (other streams, other threads) race; serialise
+ * them. Returns ADEPT_EINVAL for a null pointer, a bad material, a non-positive cut or
+ * n_materials outside 1..ADEPT_NOALLOC_MAX_MATERIALS, ADEPT_ECUDA if the launch fails. */
+#define ADEPT_NOALLOC_MAX_MATERIALS 4
+int adept_build_tables_noalloc(const adept_material* materials, int32_t n_materials, double range_cut_mm,
+                               double* dev_tables, double* dev_cuts, void* stream);
+
 const char* adept_last_error(const adept_ctx* ctx);
 void adept_destroy(adept_ctx* ctx);
 

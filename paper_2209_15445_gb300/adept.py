@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH):
             "adept_probe_inverse_range": [vp, i32, i32, i32, dp, sz, dp],
             "adept_probe_distance": [vp, i32, dp, dp, i32p, dp, i32p, sz, dp, i32p],
             "adept_probe_sample": [vp, i32, i32, i32, C.c_double, u32, sz, dp],
+            "adept_build_tables_noalloc": [C.POINTER(adept_material), i32, C.c_double, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -250,6 +251,12 @@ def adept_probe_distance(h, prec, pos, d, vol, T, q):
     nx = np.zeros(n, np.int32)
     rc = load().adept_probe_distance(h, prec, _dp(pos), _dp(d), _i32p(vol), _dp(T), _i32p(q), n, _dp(s), _i32p(nx))
     return rc, s, nx
+
+
+def adept_build_tables_noalloc(materials, range_cut_mm, dev_tables_ptr, dev_cuts_ptr, stream):
+    """Forward to the allocation-free table build; materials is a list of workloads.Material."""
+    arr = (adept_material * len(materials))(*[adept_material(m.Z, m.A, m.density, m.I_eV) for m in materials])
+    return load().adept_build_tables_noalloc(arr, len(materials), range_cut_mm, dev_tables_ptr, dev_cuts_ptr, stream)
 
 
 def adept_probe_sample(h, which, m, prec, E, event, n):
