@@ -99,7 +99,7 @@ typedef struct {
   int32_t block_size;         /* threads per block of the step kernel [256] */
   int32_t blocks_per_sm;      /* transport-kernel variant compiled for 1..4 resident
                                  256-thread blocks per SM (register cap 255/128/85/64); the
-                                 persistent grid is SMs x its occupancy [4 split, 1 FP64] */
+                                 persistent grid is SMs x its occupancy [3 split, 2 FP64] */
   int32_t graph_generations;  /* generations per captured CUDA graph; 0 = launch each
                                  generation and read the queue sizes after it [32] */
   uint32_t seed;              /* Philox key word 0 [1] */

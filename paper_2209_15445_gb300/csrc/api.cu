@@ -345,7 +345,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     c->block = o.block_size;
     for (int sp = 0; sp < 3; ++sp) {
       int mb = o.blocks_per_sm_species[sp] > 0 ? o.blocks_per_sm_species[sp] : o.blocks_per_sm;
-      if (mb <= 0) mb = o.precision ? 4 : 1;
+      if (mb <= 0) mb = o.precision ? 3 : 2;
       c->minb[sp] = std::min(4, mb);
       int bps = transport_max_blocks_per_sm(o.precision, sp, c->minb[sp], o.block_size);
       c->grid[sp] = sms * (bps < 1 ? 1 : bps);

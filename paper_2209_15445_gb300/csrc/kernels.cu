@@ -247,28 +247,31 @@ template <> __device__ __forceinline__ const float* range_nodes<float>(const Tab
 
 __device__ __forceinline__ bool on(uint32_t mask, uint32_t bit) { return mask == 0u || (mask & bit); }
 
-// One step of one track of species S (0 gamma, 1 e-, 2 e+) -- paper Sec. 3: every live
-// track advances by one step per generation. On return: alive = the track goes to the
-// next queue of its species with state t; sec holds up to two secondaries (sp < 0 for
-// one deposited below the tracking cut); dep is the energy to score in bin dep_bin.
-// Physics runs in R; positions, boundary distances and energies keep FP64 where it counts.
+enum Outcome { kDead = 0, kAlive = 1, kInteract = 2 };
+
+// Phase A of one step of one track of species S (0 gamma, 1 e-, 2 e+) -- paper Sec. 3:
+// every live track advances by one step per generation. Cross sections and range at the
+// pre-step energy (S2), sampled interaction length (S3), step limit (S4), boundary
+// distance (S5/S6), move, continuous loss (S7) and boundary crossing (S8). A step that
+// ends in a discrete interaction returns kInteract with the chosen process; the
+// interaction itself (S9) runs later on a full warp. dep is the energy to score in
+// dep_bin; sec receives the two photons of a positron that stops.
 template <class R, int S>
-__device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& alive, Ixn<R>& sec, double& dep,
-                                           int& dep_bin, uint32_t& pstep) {
+__device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>& sec, double& dep, int& dep_bin,
+                                              uint32_t& pstep, int& proc) {
   constexpr int q = S == 1 ? -1 : (S == 2 ? 1 : 0);
   const double rest = S == 2 ? 2.0 * kMe : 0.0;
   const int vol = (int)(t.nav & 0xFFFFu);
   uint32_t vac = t.nav >> 16;
   const int m = __ldg(P.geo.vol_mat + vol);
   dep_bin = __ldg(P.geo.vol_bin + vol);
-  alive = false;
   sec.n = 0;
   dep = 0.0;
   const uint32_t step = t.step;
   pstep = step;
-  if (step >= P.max_steps) { atomicAdd(P.evt.killed + t.ev, t.E + rest); return; }
+  if (step >= P.max_steps) { atomicAdd(P.evt.killed + t.ev, t.E + rest); return kDead; }
   if (m < 0) {
-    if (vac >= P.max_vac) { atomicAdd(P.evt.killed + t.ev, t.E + rest); return; }
+    if (vac >= P.max_vac) { atomicAdd(P.evt.killed + t.ev, t.E + rest); return kDead; }
     ++vac;
   } else {
     vac = 0;
@@ -279,7 +282,7 @@ __device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& ali
   if (Er < tcut) {
     dep = t.E;
     if (S == 2) annihilate_at_rest<R>(rs, sec);
-    return;
+    return kDead;
   }
   R u0, u1;
   rs.block0(&u0, &u1);
@@ -346,24 +349,37 @@ __device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& ali
       dep += t.E;
       t.E = 0.0;
       if (S == 2) annihilate_at_rest<R>(rs, sec);
-      return;
+      return kDead;
     }
   }
   // S8: boundary crossing
   if (boundary) {
-    if (next < 0) { atomicAdd(P.evt.leaked + t.ev, t.E + rest); return; }
+    if (next < 0) { atomicAdd(P.evt.leaked + t.ev, t.E + rest); return kDead; }
     t.nav = (uint32_t)next | (vac << 16);
-    alive = true;
-    return;
+    return kAlive;
   }
   t.nav = (uint32_t)vol | (vac << 16);
-  // S9: discrete interaction, process chosen with u1 over the fixed order
+  // S9 (deferred): the process is chosen with u1 over the fixed order
   const R xs = u1 * stot;
-  int proc = (S == 1) ? 1 : 2;
+  proc = (S == 1) ? 1 : 2;
   if (xs < sg0) proc = 0;
   else if (xs < sg0 + sg1) proc = 1;
+  return kInteract;
+}
+
+// Phase B: the discrete interaction (S9) of a track queued by phase A. Its random stream
+// is rebuilt from (event, id, step): block 0 was consumed in phase A, the models draw
+// from block 1 on. Returns whether the parent survives (with its new state in t).
+template <class R, int S>
+__device__ __forceinline__ bool step_interact(const Params& P, Trk<R>& t, uint32_t pstep, int proc, Ixn<R>& sec,
+                                              double& dep) {
+  const int m = __ldg(P.geo.vol_mat + (int)(t.nav & 0xFFFFu));
+  Stream<R> rs(P.seed, __ldg(P.evt.key + t.ev), t.id, pstep);
   const double Tc = __ldg(P.tab.Tc + m), kc = __ldg(P.tab.kc + m);
+  const R tcut = (R)P.tcut;
   sec.happened = false;
+  sec.n = 0;
+  dep = 0.0;
   if (S == 0) {
     if (proc == 0) compton<R>(rs, t.E, t.u, sec);
     else if (proc == 1) pair<R>(rs, t.E, t.u, sec);
@@ -376,44 +392,32 @@ __device__ __forceinline__ void step_track(const Params& P, Trk<R>& t, bool& ali
     else if (proc == 1) brem<R>(rs, t.E, kc, t.u, sec);
     else annihilate<R>(rs, t.E, t.u, sec);
   }
-  if (!sec.happened) { sec.n = 0; alive = true; return; }
+  if (!sec.happened) { sec.n = 0; return true; }
   // secondaries other than positrons below the tracking cut deposit locally
 #pragma unroll
   for (int k = 0; k < 2; ++k)
     if (k < sec.n && sec.sp[k] != 2 && to_r<R>(sec.E[k]) < tcut) { dep += sec.E[k]; sec.sp[k] = -1; }
-  if (!sec.parent_alive) return;
+  if (!sec.parent_alive) return false;
   t.E = sec.parent_E;
   t.u[0] = sec.pd[0]; t.u[1] = sec.pd[1]; t.u[2] = sec.pd[2];
-  if (S == 0 && to_r<R>(t.E) < tcut) { dep += t.E; return; }
-  alive = true;
+  if (S == 0 && to_r<R>(t.E) < tcut) { dep += t.E; return false; }
+  return true;
 }
 
-// One warp advances up to 32 consecutive tracks of species S and appends the results
-// (the surviving track and its secondaries) to the next queues with one atomic per
-// species per warp (S9/S11: warp-aggregated secondary allocation).
+__device__ __forceinline__ void score(const Params& P, uint32_t ev, int bin, double dep) {
+  if (bin >= 0 && __double_as_longlong(dep) != 0) atomicAdd(P.evt.edep + (size_t)ev * P.geo.n_bins + bin, dep);
+}
+
+// Warp-aggregated appends (S9/S11): every lane of the warp calls this; a lane passes the
+// surviving track (alive) and up to two secondaries, and gets consecutive slots of the
+// next queues through one atomic per species per warp.
 template <class R, int S>
-__device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, uint32_t n,
-                                         unsigned long long* nsteps, unsigned long long* ncreated) {
+__device__ __forceinline__ void emit(const Params& P, int p, const Trk<R>& t, bool alive, const Ixn<R>& sec,
+                                     uint32_t pstep, unsigned long long* ncreated) {
   const int lane = threadIdx.x & 31;
-  const uint32_t i = base + lane;
-  const bool active = i < n;
-  Trk<R> t;
-  t.nav = 0; t.ev = 0; t.id = 0; t.E = 0.0;
-  bool alive = false;
-  Ixn<R> sec;
-  sec.n = 0;
-  double dep = 0.0;
-  int dep_bin = -1;
-  uint32_t pstep = 0;
-  if (active) {
-    load_track<R>(P.q[p][S], i, t);
-    step_track<R, S>(P, t, alive, sec, dep, dep_bin, pstep);
-    // S10: score the step's deposit in (event, layer, material)
-    if (dep_bin >= 0 && __double_as_longlong(dep) != 0) atomicAdd(P.evt.edep + (size_t)t.ev * P.geo.n_bins + dep_bin, dep);
-  }
   const uint32_t lt = (1u << lane) - 1u;
-  const bool f1 = active && sec.n > 0 && sec.sp[0] >= 0;
-  const bool f2 = active && sec.n > 1 && sec.sp[1] >= 0;
+  const bool f1 = sec.n > 0 && sec.sp[0] >= 0;
+  const bool f2 = sec.n > 1 && sec.sp[1] >= 0;
   const int s1 = f1 ? sec.sp[0] : -1, s2 = f2 ? sec.sp[1] : -1;
   uint32_t b0[3], b1[3], b2[3], wbase[3];
 #pragma unroll
@@ -425,11 +429,8 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
     uint32_t bk = 0;
     if (lane == 0 && cnt) bk = atomicAdd(&P.ctrl->count[p ^ 1][k], cnt);
     wbase[k] = __shfl_sync(0xFFFFFFFFu, bk, 0);
+    ncreated[k] += __popc(b1[k]) + __popc(b2[k]);
   }
-  const uint32_t act = __ballot_sync(0xFFFFFFFFu, active);
-  nsteps[S] += __popc(act);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) ncreated[k] += __popc(b1[k]) + __popc(b2[k]);
   const TrackSoA* nq = P.q[p ^ 1];
   // pick entry k of a 3-array without dynamic indexing (which would place it in local memory)
   auto pick = [](const uint32_t* a, int k) { return k == 0 ? a[0] : (k == 1 ? a[1] : a[2]); };
@@ -461,6 +462,85 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
   }
 }
 
+// Per-warp ring of tracks waiting for their discrete interaction (64 entries: phase A of
+// one tile adds at most 32 to fewer than 32 waiting, so nothing is overwritten before it
+// is processed). Interactions then run 32 at a time on a full warp instead of on the few
+// lanes of each tile that happened to interact.
+constexpr int kRing = 64;
+template <class R> struct WarpRing {
+  double x[kRing], y[kRing], z[kRing], E[kRing];
+  unsigned long long id[kRing];
+  R ux[kRing], uy[kRing], uz[kRing];
+  uint32_t ev[kRing], pstep[kRing], nav[kRing], proc[kRing];
+};
+
+template <class R, int S>
+__device__ __forceinline__ void drain(const Params& P, int p, WarpRing<R>& ring, uint32_t head, uint32_t count,
+                                      unsigned long long* ncreated) {
+  const int lane = threadIdx.x & 31;
+  const bool have = (uint32_t)lane < count;
+  Trk<R> t;
+  t.nav = 0; t.ev = 0; t.id = 0; t.E = 0.0; t.step = 0;
+  uint32_t pstep = 0;
+  Ixn<R> sec;
+  sec.n = 0;
+  bool alive = false;
+  if (have) {
+    const uint32_t j = (head + lane) & (kRing - 1);
+    t.x = ring.x[j]; t.y = ring.y[j]; t.z = ring.z[j]; t.E = ring.E[j];
+    t.u[0] = ring.ux[j]; t.u[1] = ring.uy[j]; t.u[2] = ring.uz[j];
+    t.id = ring.id[j]; t.ev = ring.ev[j]; t.nav = ring.nav[j];
+    pstep = ring.pstep[j];
+    t.step = pstep + 1;
+    double dep = 0.0;
+    alive = step_interact<R, S>(P, t, pstep, (int)ring.proc[j], sec, dep);
+    score(P, t.ev, __ldg(P.geo.vol_bin + (int)(t.nav & 0xFFFFu)), dep);
+  }
+  __syncwarp();
+  emit<R, S>(P, p, t, alive, sec, pstep, ncreated);
+}
+
+// One warp takes 32 consecutive tracks of species S: phase A for each, appends the
+// survivors, queues the interactions and runs full warps of them as they accumulate.
+template <class R, int S>
+__device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, uint32_t n, WarpRing<R>& ring,
+                                         uint32_t& head, uint32_t& tail, unsigned long long* nsteps,
+                                         unsigned long long* ncreated) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t i = base + lane;
+  const bool active = i < n;
+  Trk<R> t;
+  t.nav = 0; t.ev = 0; t.id = 0; t.E = 0.0;
+  Ixn<R> sec;
+  sec.n = 0;
+  uint32_t pstep = 0;
+  int outcome = kDead, proc = 0;
+  if (active) {
+    load_track<R>(P.q[p][S], i, t);
+    double dep = 0.0;
+    int dep_bin = -1;
+    outcome = step_transport<R, S>(P, t, sec, dep, dep_bin, pstep, proc);
+    // S10: score the step's deposit in (event, layer, material)
+    score(P, t.ev, dep_bin, dep);
+  }
+  nsteps[S] += __popc(__ballot_sync(0xFFFFFFFFu, active));
+  emit<R, S>(P, p, t, outcome == kAlive, sec, pstep, ncreated);
+  const uint32_t need = __ballot_sync(0xFFFFFFFFu, outcome == kInteract);
+  if (outcome == kInteract) {
+    const uint32_t j = (tail + __popc(need & ((1u << lane) - 1u))) & (kRing - 1);
+    ring.x[j] = t.x; ring.y[j] = t.y; ring.z[j] = t.z; ring.E[j] = t.E;
+    ring.ux[j] = t.u[0]; ring.uy[j] = t.u[1]; ring.uz[j] = t.u[2];
+    ring.id[j] = t.id; ring.ev[j] = t.ev; ring.nav[j] = t.nav; ring.pstep[j] = pstep; ring.proc[j] = (uint32_t)proc;
+  }
+  tail += __popc(need);
+  __syncwarp();
+  while (tail - head >= 32u) {
+    drain<R, S>(P, p, ring, head, 32u, ncreated);
+    head += 32u;
+    __syncwarp();
+  }
+}
+
 // One generation of one species (paper Sec. 3: TransportElectrons, TransportPositrons and
 // TransportGammas). Persistent launch: each warp takes 32-track tiles of the current queue.
 // The three run back to back per generation (e-, e+, gamma); the last block of the gamma
@@ -468,6 +548,7 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
 template <class R, int S, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
   __shared__ unsigned long long s_steps, s_created[3];
+  __shared__ WarpRing<R> rings[8];
   const uint32_t gen = __ldcg(&P.ctrl->gen);
   const int p = gen & 1;
   if (threadIdx.x == 0) { s_steps = 0; s_created[0] = s_created[1] = s_created[2] = 0; }
@@ -476,9 +557,12 @@ __global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
   const uint32_t n = min(__ldcg(&P.ctrl->count[p][S]), P.cap);
   const uint32_t tiles = (n + 31) >> 5;
   const uint32_t wpb = blockDim.x >> 5;
+  WarpRing<R>& ring = rings[threadIdx.x >> 5];
+  uint32_t head = 0, tail = 0;
   unsigned long long nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
   for (uint32_t tile = blockIdx.x * wpb + (threadIdx.x >> 5); tile < tiles; tile += gridDim.x * wpb)
-    run_tile<R, S>(P, p, tile << 5, n, nsteps, ncreated);
+    run_tile<R, S>(P, p, tile << 5, n, ring, head, tail, nsteps, ncreated);
+  if (tail != head) drain<R, S>(P, p, ring, head, tail - head, ncreated);
   if ((threadIdx.x & 31) == 0) {
     if (nsteps[S]) atomicAdd(&s_steps, nsteps[S]);
     for (int k = 0; k < 3; ++k)
