@@ -39,6 +39,12 @@ template <> struct M<double> {
   static __device__ __forceinline__ double sin(double x) { return ::sin(x); }
   static __device__ __forceinline__ double floor(double x) { return ::floor(x); }
   static __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
+  // "fast" forms: in FP64 the same correctly rounded functions
+  static __device__ __forceinline__ double flog(double x) { return ::log(x); }
+  static __device__ __forceinline__ double fexp(double x) { return ::exp(x); }
+  static __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+  static __device__ __forceinline__ void fsincos(double x, double* s, double* c) { ::sincos(x, s, c); }
+  static __device__ __forceinline__ double fcos(double x) { return ::cos(x); }
   static __host__ __device__ constexpr double big() { return 1e300; }
   static __host__ __device__ constexpr double turn_tol() { return 0.0; }
 };
@@ -55,6 +61,14 @@ template <> struct M<float> {
   static __device__ __forceinline__ float sin(float x) { return ::sinf(x); }
   static __device__ __forceinline__ float floor(float x) { return ::floorf(x); }
   static __device__ __forceinline__ float fabs(float x) { return ::fabsf(x); }
+  // fast forms for the sampling arithmetic (a few ulp; the split form is validated
+  // statistically): hardware approximations of log, exp, sin/cos and division. The table
+  // grid position, the helix and the boundary geometry keep the accurate functions.
+  static __device__ __forceinline__ float flog(float x) { return __logf(x); }
+  static __device__ __forceinline__ float fexp(float x) { return __expf(x); }
+  static __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ void fsincos(float x, float* s, float* c) { __sincosf(x, s, c); }
+  static __device__ __forceinline__ float fcos(float x) { return __cosf(x); }
   static __host__ __device__ constexpr float big() { return 1e30f; }
   // a helix root within this many radians below a full turn is the current point seen
   // through FP32 rounding of the phase: treat it as an immediate crossing
@@ -248,8 +262,8 @@ __device__ __forceinline__ R inverse_range(const R* nodes, R r, int hint_hi) {
     if (__ldg(nodes + mid) <= r) lo = mid; else hi = mid;
   }
   const R a = __ldg(nodes + lo), b = __ldg(nodes + lo + 1);
-  const R t = (r - a) / (b - a);
-  return M<R>::exp(Grid<R>::lnEmin() + ((R)lo + t) * Grid<R>::dlog());
+  const R t = M<R>::fdiv(r - a, b - a);
+  return M<R>::fexp(Grid<R>::lnEmin() + ((R)lo + t) * Grid<R>::dlog());
 }
 
 // ---------------------------------------------------------------- direction helpers
@@ -260,13 +274,13 @@ __device__ __forceinline__ void rotate_to(R ux, R uy, R uz, R cost, R phi, R* ox
   s2 = s2 < (R)0 ? (R)0 : s2;
   const R sint = M<R>::sqrt(s2);
   R sp, cp;
-  M<R>::sincos(phi, &sp, &cp);
+  M<R>::fsincos(phi, &sp, &cp);
   const R l0 = sint * cp, l1 = sint * sp, l2 = cost;
   const R up2 = ux * ux + uy * uy;
   if (up2 > (R)0) {
     const R up = M<R>::sqrt(up2);
-    *ox = (ux * uz * l0 - uy * l1) / up + ux * l2;
-    *oy = (uy * uz * l0 + ux * l1) / up + uy * l2;
+    *ox = M<R>::fdiv(ux * uz * l0 - uy * l1, up) + ux * l2;
+    *oy = M<R>::fdiv(uy * uz * l0 + ux * l1, up) + uy * l2;
     *oz = -up * l0 + uz * l2;
   } else if (uz >= (R)0) {
     *ox = l0; *oy = l1; *oz = l2;
@@ -278,7 +292,7 @@ __device__ __forceinline__ void rotate_to(R ux, R uy, R uz, R cost, R phi, R* ox
 template <class R>
 __device__ __forceinline__ void unit(R* x, R* y, R* z) {
   const R n = M<R>::sqrt(*x * *x + *y * *y + *z * *z);
-  *x /= n; *y /= n; *z /= n;
+  *x = M<R>::fdiv(*x, n); *y = M<R>::fdiv(*y, n); *z = M<R>::fdiv(*z, n);
 }
 
 // ---------------------------------------------------------------- interactions
@@ -300,15 +314,15 @@ template <class R>
 __device__ void compton(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
   const R Er = to_r<R>(E);
   const R kap = Er / (R)kMe;
-  const R e0 = (R)1 / ((R)1 + (R)2 * kap);
+  const R e0 = M<R>::fdiv((R)1, (R)1 + (R)2 * kap);
   const R a1 = M<R>::log1p((R)2 * kap);
   const R a2 = (R)0.5 * ((R)1 - e0 * e0);
   R eps = 1, t = 0;
   for (int it = 0; it < kMaxRej; ++it) {
     const R r1 = st.next(), r2 = st.next(), r3 = st.next();
-    eps = (r1 * (a1 + a2) < a1) ? M<R>::exp(-a1 * r2) : M<R>::sqrt(e0 * e0 + ((R)1 - e0 * e0) * r2);
-    t = ((R)1 - eps) / (kap * eps);
-    const R g = (R)1 - eps * (t * ((R)2 - t)) / ((R)1 + eps * eps);
+    eps = (r1 * (a1 + a2) < a1) ? M<R>::fexp(-a1 * r2) : M<R>::sqrt(e0 * e0 + ((R)1 - e0 * e0) * r2);
+    t = M<R>::fdiv((R)1 - eps, kap * eps);
+    const R g = (R)1 - M<R>::fdiv(eps * (t * ((R)2 - t)), (R)1 + eps * eps);
     if (r3 < g) break;
   }
   const R phi = (R)(2.0 * kPi) * st.next();
@@ -332,7 +346,7 @@ __device__ void pair(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
   r.happened = false;
   const R Er = to_r<R>(E);
   if (!(Er > (R)(2.0 * kMe))) return;
-  const R a = (R)kMe / Er;
+  const R a = M<R>::fdiv((R)kMe, Er);
   R x = (R)0.5;
   for (int it = 0; it < kMaxRej; ++it) {
     const R r1 = st.next(), r2 = st.next();
@@ -347,10 +361,10 @@ __device__ void pair(Stream<R>& st, double E, const R u[3], Ixn<R>& r) {
   r.n = 2;
   r.sp[0] = 2;
   r.E[0] = Tp;
-  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)kMe / (to_r<R>(Tp) + (R)kMe)), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
+  rotate_to<R>(u[0], u[1], u[2], M<R>::fcos(M<R>::fdiv((R)kMe, to_r<R>(Tp) + (R)kMe)), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
   r.sp[1] = 1;
   r.E[1] = Tm;
-  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)kMe / (to_r<R>(Tm) + (R)kMe)), phi + (R)kPi, &r.d[1][0], &r.d[1][1], &r.d[1][2]);
+  rotate_to<R>(u[0], u[1], u[2], M<R>::fcos(M<R>::fdiv((R)kMe, to_r<R>(Tm) + (R)kMe)), phi + (R)kPi, &r.d[1][0], &r.d[1][1], &r.d[1][2]);
 }
 
 template <class R>
@@ -367,7 +381,7 @@ __device__ __forceinline__ void photo(double E, const R u[3], Ixn<R>& r) {
 template <class R>
 __device__ void delta_ray(Stream<R>& st, double T, double Td, const R u[3], Ixn<R>& r) {
   const R Tr = to_r<R>(T), Tdr = to_r<R>(Td), m2 = (R)(2.0 * kMe);
-  R cd = M<R>::sqrt(Tdr * (Tr + m2) / (Tr * (Tdr + m2)));
+  R cd = M<R>::sqrt(M<R>::fdiv(Tdr * (Tr + m2), Tr * (Tdr + m2)));
   cd = cd > (R)1 ? (R)1 : cd;
   const R phi = (R)(2.0 * kPi) * st.next();
   R dx, dy, dz;
@@ -392,15 +406,15 @@ __device__ void moller(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>&
   r.happened = false;
   const R Tr = to_r<R>(T);
   if (!(Tr > (R)2 * to_r<R>(Tc))) return;
-  const R g = Tr / (R)kMe + (R)1;
-  const R gg = ((R)2 * g - (R)1) / (g * g);
-  const R ec = to_r<R>(Tc) / Tr, em = (R)0.5;
+  const R g = M<R>::fdiv(Tr, (R)kMe) + (R)1;
+  const R gg = M<R>::fdiv((R)2 * g - (R)1, g * g);
+  const R ec = M<R>::fdiv(to_r<R>(Tc), Tr), em = (R)0.5;
   const R gmax = (R)2 + (R)0.25 * ((R)1 - gg);
   R eps = ec;
   for (int it = 0; it < kMaxRej; ++it) {
     const R r1 = st.next(), r2 = st.next();
-    eps = ec * em / (em - (em - ec) * r1);
-    const R q = eps / ((R)1 - eps);
+    eps = M<R>::fdiv(ec * em, em - (em - ec) * r1);
+    const R q = M<R>::fdiv(eps, (R)1 - eps);
     const R f = (R)1 + q * q + ((R)1 - gg) * eps * eps - gg * q;
     if (r2 * gmax < f) break;
   }
@@ -413,18 +427,18 @@ __device__ void bhabha(Stream<R>& st, double T, double Tc, const R u[3], Ixn<R>&
   r.happened = false;
   const R Tr = to_r<R>(T);
   if (!(Tr > to_r<R>(Tc))) return;
-  const R tau = Tr / (R)kMe;
+  const R tau = M<R>::fdiv(Tr, (R)kMe);
   const R g = tau + (R)1;
-  const R b2 = tau * (tau + (R)2) / (g * g);
-  const R y = (R)1 / (g + (R)1);
+  const R b2 = M<R>::fdiv(tau * (tau + (R)2), g * g);
+  const R y = M<R>::fdiv((R)1, g + (R)1);
   const R y12 = (R)1 - (R)2 * y;
   const R B1 = (R)2 - y * y, B2 = y12 * ((R)3 + y * y), B4 = y12 * y12 * y12;
   const R B3 = B4 + y12 * y12;
-  const R ec = to_r<R>(Tc) / Tr;
+  const R ec = M<R>::fdiv(to_r<R>(Tc), Tr);
   R eps = ec;
   for (int it = 0; it < kMaxRej; ++it) {
     const R r1 = st.next(), r2 = st.next();
-    eps = ec / ((R)1 - ((R)1 - ec) * r1);
+    eps = M<R>::fdiv(ec, (R)1 - ((R)1 - ec) * r1);
     const R gf = (R)1 - b2 * eps * (B1 - eps * (B2 - eps * (B3 - eps * B4)));
     if (r2 < gf) break;
   }
@@ -438,12 +452,12 @@ __device__ void brem(Stream<R>& st, double T, double kc, const R u[3], Ixn<R>& r
   const R Tr = to_r<R>(T), kcR = to_r<R>(kc);
   if (!(Tr > kcR)) return;
   const R Ef = Tr + (R)kMe;
-  const R lr = M<R>::log(Tr / kcR);
+  const R lr = M<R>::flog(M<R>::fdiv(Tr, kcR));
   R k = kcR;
   for (int it = 0; it < kMaxRej; ++it) {
     const R r1 = st.next(), r2 = st.next();
-    k = kcR * M<R>::exp(lr * r1);
-    const R y = k / Ef;
+    k = kcR * M<R>::fexp(lr * r1);
+    const R y = M<R>::fdiv(k, Ef);
     if (r2 < (R)1 - y + (R)0.75 * y * y) break;
   }
   const double kd = (k >= Tr) ? T : to_d<R>(k);  // FP32 rounding of kc (T/kc)^r can reach T
@@ -455,7 +469,7 @@ __device__ void brem(Stream<R>& st, double T, double kc, const R u[3], Ixn<R>& r
   r.n = 1;
   r.sp[0] = 0;
   r.E[0] = kd;
-  rotate_to<R>(u[0], u[1], u[2], M<R>::cos((R)kMe / Ef), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
+  rotate_to<R>(u[0], u[1], u[2], M<R>::fcos(M<R>::fdiv((R)kMe, Ef)), phi, &r.d[0][0], &r.d[0][1], &r.d[0][2]);
 }
 
 // Heitler annihilation in flight: eps = E1/(T+2m) from 1/eps on [eps_min, eps_max],
@@ -463,23 +477,23 @@ __device__ void brem(Stream<R>& st, double T, double kc, const R u[3], Ixn<R>& r
 template <class R>
 __device__ void annihilate(Stream<R>& st, double T, const R u[3], Ixn<R>& r) {
   const R Tr = to_r<R>(T);
-  const R tau = Tr / (R)kMe;
+  const R tau = M<R>::fdiv(Tr, (R)kMe);
   const R g = tau + (R)1;
-  const R sq = M<R>::sqrt(tau / (tau + (R)2));
+  const R sq = M<R>::sqrt(M<R>::fdiv(tau, tau + (R)2));
   const R emin = (R)0.5 * ((R)1 - sq), emax = (R)0.5 * ((R)1 + sq);
-  const R lr = M<R>::log(emax / emin);
+  const R lr = M<R>::flog(M<R>::fdiv(emax, emin));
   const R gp1 = g + (R)1;
   R eps = (R)0.5;
   for (int it = 0; it < kMaxRej; ++it) {
     const R r1 = st.next(), r2 = st.next();
-    eps = emin * M<R>::exp(lr * r1);
-    const R gf = (R)1 - eps + ((R)2 * g * eps - (R)1) / (eps * gp1 * gp1);
+    eps = emin * M<R>::fexp(lr * r1);
+    const R gf = (R)1 - eps + M<R>::fdiv((R)2 * g * eps - (R)1, eps * gp1 * gp1);
     if (r2 < gf) break;
   }
   const double Etot = T + 2.0 * kMe;
   const double E1 = to_d<R>(eps * to_r<R>(Etot));
   const double E2 = Etot - E1;
-  R c1 = (eps * gp1 - (R)1) / (eps * M<R>::sqrt(tau * (tau + (R)2)));
+  R c1 = M<R>::fdiv(eps * gp1 - (R)1, eps * M<R>::sqrt(tau * (tau + (R)2)));
   c1 = c1 > (R)1 ? (R)1 : (c1 < (R)-1 ? (R)-1 : c1);
   const R phi = (R)(2.0 * kPi) * st.next();
   r.happened = true;
@@ -505,7 +519,7 @@ __device__ void annihilate_at_rest(Stream<R>& st, Ixn<R>& r) {
   s2 = s2 < (R)0 ? (R)0 : s2;
   const R s = M<R>::sqrt(s2);
   R sp, cp;
-  M<R>::sincos(phi, &sp, &cp);
+  M<R>::fsincos(phi, &sp, &cp);
   r.happened = true;
   r.parent_alive = false;
   r.n = 2;
@@ -520,7 +534,7 @@ __device__ void annihilate_at_rest(Stream<R>& st, Ixn<R>& r) {
 // 0 is r < bnd[0], volume v is bnd[v-1] <= r < bnd[v], |z| <= half_z. next = -1 leaves.
 template <class R>
 __device__ __forceinline__ R slab_wall(R p, R u, R H) {
-  return u > (R)0 ? (H - p) / u : (u < (R)0 ? (-H - p) / u : M<R>::big());
+  return u > (R)0 ? M<R>::fdiv(H - p, u) : (u < (R)0 ? M<R>::fdiv(-H - p, u) : M<R>::big());
 }
 
 // Path lengths are of type R; the FP64 work is the distance to a plane (z_plane - z)
@@ -532,10 +546,10 @@ __device__ R straight_distance(const GeoView& g, double x, double y, double z, c
   int nx = vol;
   if (g.kind == 0) {
     if (u[2] > (R)0) {
-      s = to_r<R>(__ldg(g.bnd + vol + 1) - z) / u[2];
+      s = M<R>::fdiv(to_r<R>(__ldg(g.bnd + vol + 1) - z), u[2]);
       nx = (vol + 1 < g.n_vol) ? vol + 1 : -1;
     } else if (u[2] < (R)0) {
-      s = to_r<R>(__ldg(g.bnd + vol) - z) / u[2];
+      s = M<R>::fdiv(to_r<R>(__ldg(g.bnd + vol) - z), u[2]);
       nx = vol - 1;
     }
     const R H = (R)g.half_xy;

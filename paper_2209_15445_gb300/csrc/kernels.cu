@@ -316,7 +316,7 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
   sg2 = sg2 < (R)0 ? (R)0 : sg2;
   const R stot = sg0 + sg1 + sg2;
   // S3/S4: sampled interaction length and the range-based step limit
-  R s_phys = stot > (R)0 ? -M<R>::log(u0) / stot : M<R>::big();
+  R s_phys = stot > (R)0 ? M<R>::fdiv(-M<R>::flog(u0), stot) : M<R>::big();
   if (q != 0 && m >= 0) {
     const R smax = (Rr <= (R)kRhoF) ? Rr : ((R)kAlphaR * Rr > (R)kRhoF ? (R)kAlphaR * Rr : (R)kRhoF);
     if (smax < s_phys) s_phys = smax;
