@@ -69,6 +69,9 @@ def args_parse():
     ap.add_argument("--arena-gb", type=float, default=10.0)
     ap.add_argument("--bps", type=int, default=0, help="transport-kernel blocks/SM variant (0 = library default)")
     ap.add_argument("--bps-species", type=str, default="", help="per-species variants gamma,e-,e+")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c2 (default) is the headline line; the others are the configuration studies")
+    ap.add_argument("--seconds", type=float, default=20.0, help="serving workload duration")
     return ap.parse_args()
 
 
@@ -308,7 +311,7 @@ def run_ours(a):
                 "dtype": "f32/f64" if a.precision else "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "events": n, "E_MeV": E, "precision": "split" if a.precision else "fp64",
                            "graph_generations": a.graph, "block": tr.options.block_size or 256,
-                           "blocks_per_sm_variant": a.bps or (2 if a.precision else 1),
+                           "blocks_per_sm_variant": a.bps or (3 if a.precision else 2),
                            "l2": "track queues (GBs) exceed L2; 256 MB buffer written between steps"},
                 "showers_per_s": showers, "steps_per_shower": steps / (a.steps * n),
                 "energy_conserved": bool(edep_ok), "roofline": roof, "cpu_baseline": base, "e2e": e2e,
@@ -320,10 +323,130 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def _line(a, workload, value, t_s, extra):
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * t_s / max(1, a.steps), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/f64" if a.precision else "f64", "data": "synthetic",
+            "config": {"workload": workload, **extra.pop("config", {})}, **extra}
+
+
+def run_study(a):
+    """Configuration studies (not the headline line): c1 plain FP64 one event per launch,
+    c3 batched mixed primaries in 1 T, c4 barrel in 3.8 T, c5 serving with 16 producers."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2209_15445_gb300 import adept as A
+    from paper_2209_15445_gb300 import build as B
+    from paper_2209_15445_gb300 import workloads as W
+
+    B.build()
+    torch.cuda.set_device(0)
+    if a.workload == "c1":
+        # plain FP64, one event per transport, one generation per launch with the queue
+        # sizes read back after each (the paper's small-batch form)
+        tr = A.Transport(W.slab_calorimeter(), precision=0, arena_bytes=1 << 30, graph_generations=0)
+        prim = W.electrons(100, 1000.0)
+        arrs = [A.tracks_array(prim.take([i])) for i in range(100)]
+        for k in range(a.warmup):
+            rid = tr.submit(arrs[k]); tr.transport(); tr.result(rid, 1)
+        s0 = tr.stats(); t0 = time.perf_counter()
+        for k in range(100):
+            rid = tr.submit(arrs[k]); tr.transport(); tr.result(rid, 1)
+        dt = time.perf_counter() - t0; s1 = tr.stats()
+        st = sum(s1.steps) - sum(s0.steps)
+        a.precision = 0
+        print(json.dumps(_line(a, "100 x 1 GeV e-, slab, plain FP64, one event per transport, one generation per launch",
+                               st / dt, dt, {"showers_per_s": 100 / dt, "steps": 1, "gpu_launches": int(s1.launches - s0.launches)})))
+        return
+    if a.workload in ("c3", "c4"):
+        if a.workload == "c3":
+            geom, field, prim = W.slab_calorimeter(), 1.0, W.mixed(20000, seed=3)
+            name = "20,000 primaries 0.1-100 GeV, 50% gamma / 40% e- / 10% e+, slab, 1 T; split, batched"
+            chunks, arena = 1, 12 << 30
+        else:
+            geom, field, prim = W.barrel_calorimeter(), 3.8, W.barrel_primaries(100000, seed=4)
+            name = "100,000 e-/gamma 1-50 GeV, |eta|<1.5, 20-layer barrel, 3.8 T; split, batched in 100 requests"
+            chunks, arena = 100, 40 << 30
+        tr = A.Transport(geom, precision=a.precision, field_T=field, arena_bytes=arena, graph_generations=a.graph,
+                         flags=A.FLAG_TIME_STEPS, max_events=200000, tracks_per_MeV=0.1)
+        n = len(prim)
+        parts = [prim.take(np.arange(k * n // chunks, (k + 1) * n // chunks)) for k in range(chunks)]
+        arrs = [A.tracks_array(pp) for pp in parts]
+
+        def once():
+            ids = [tr.submit(x) for x in arrs]
+            tr.transport()
+            for rid, pp in zip(ids, parts):
+                tr.result(rid, len(pp))
+        once()
+        s0 = tr.stats(); torch.cuda.synchronize(); t0 = time.perf_counter()
+        for _ in range(a.steps):
+            once()
+        torch.cuda.synchronize(); dt = time.perf_counter() - t0; s1 = tr.stats()
+        st = sum(s1.steps) - sum(s0.steps)
+        print(json.dumps(_line(a, name, st / dt, dt / a.steps,
+                               {"showers_per_s": n * a.steps / dt, "steps_per_primary": st / (n * a.steps),
+                                "species_ms_per_step": [round((s1.species_ms[k] - s0.species_ms[k]) / a.steps, 2) for k in range(3)],
+                                "gpu_launches": int(s1.launches - s0.launches)})))
+        return
+    # c5: serving -- 16 producers in a closed loop, one driver thread running the transport
+    geom = W.barrel_calorimeter()
+    tr = A.Transport(geom, precision=a.precision, field_T=3.8, arena_bytes=24 << 30, graph_generations=8,
+                     max_events=65536, tracks_per_MeV=0.1)
+    stop = threading.Event()
+    lat, done_steps, errors = [], [0], []
+    lock = threading.Lock()
+
+    def driver():
+        while not stop.is_set():
+            rc = A.adept_transport(tr.h, 20000)
+            if rc not in (A.OK, A.ETIMEOUT):
+                errors.append(A.adept_last_error(tr.h)); return
+            if rc == A.OK:
+                time.sleep(5e-5)
+
+    def producer(k):
+        rng = np.random.default_rng(1000 + k)
+        ev = 1_000_000 * (k + 1)
+        while not stop.is_set():
+            nb = W.serving_batch_size(rng)
+            batch = W.serving_batch(nb, seed=int(rng.integers(1 << 30)), event=ev)
+            ev += 1
+            rid = tr.submit(batch)
+            while A.adept_wait(tr.h, rid, 200000) == A.ETIMEOUT:
+                if stop.is_set():
+                    return
+            out, meta = tr.result(rid, 1)
+            with lock:
+                lat.append(meta.latency_us)
+
+    th = [threading.Thread(target=driver)] + [threading.Thread(target=producer, args=(k,)) for k in range(16)]
+    s0 = tr.stats(); t0 = time.perf_counter()
+    for t in th:
+        t.start()
+    time.sleep(a.seconds)
+    stop.set()
+    for t in th:
+        t.join()
+    dt = time.perf_counter() - t0; s1 = tr.stats()
+    st = sum(s1.steps) - sum(s0.steps)
+    l = np.array(lat) if lat else np.zeros(1)
+    print(json.dumps(_line(a, "serving: 16 producers, batches of 10-10,000 e-/e+/gamma (E^-2, 10 MeV-20 GeV) on the barrel inner face, 3.8 T",
+                           st / dt, dt, {"requests": len(lat), "latency_us": {"p50": float(np.percentile(l, 50)),
+                                                                              "p99": float(np.percentile(l, 99)),
+                                                                              "mean": float(l.mean())},
+                                         "errors": errors})))
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload != "c2":
+        run_study(a)
     else:
         run_ours(a)
 
