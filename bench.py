@@ -40,10 +40,11 @@ UNIT = "tracked steps/s"
 WORKLOAD = ("10,000 x 10 GeV e- showers, 50-layer Pb 2.3 mm + lAr 5.7 mm slab calorimeter, 0.7 mm cut, "
             "no field; split precision, batched persistent launch with CUDA graphs")
 TRACK_BYTES_SPLIT = 64  # x,y,z f64 + direction 3 f32 + E f64 + id u64 + event, step, nav u32
-# DRAM bytes per tracked step of the step kernel from the committed ncu capture
-# (profiles/step_kernel_10gev_e_showers.md), valid while the kernel sources hash to NCU_SRC_HASH
-NCU_BYTES_PER_STEP = None
-NCU_SRC_HASH = None
+# DRAM bytes (read + write) per tracked step of the three transport kernels, from the ncu
+# capture of generation 60 (profiles/transport_kernels_10gev_e_showers_gen60_full.md);
+# valid while the kernel sources hash to NCU_SRC_HASH, null otherwise
+NCU_BYTES_PER_STEP = 118.0
+NCU_SRC_HASH = "a845286c7bde6026"
 
 
 def kernel_src_hash() -> str:
@@ -72,6 +73,7 @@ def args_parse():
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
                     help="c2 (default) is the headline line; the others are the configuration studies")
     ap.add_argument("--seconds", type=float, default=20.0, help="serving workload duration")
+    ap.add_argument("--genlog", default="", help="write the per-generation queue sizes of the last step here")
     return ap.parse_args()
 
 
@@ -226,6 +228,8 @@ def run_ours(a):
 
     for _ in range(a.warmup):
         step_device()
+    if a.genlog:
+        A.adept_reset_generation_log(tr.h)
     s0 = tr.stats()
     barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
@@ -239,6 +243,9 @@ def run_ours(a):
             ev[k][1].record(tr.stream)
         barrier()
     s1 = tr.stats()
+    if a.genlog:
+        nlog, log = A.adept_get_generation_log(tr.h)
+        np.savetxt(a.genlog, log, fmt="%d", header="gamma e- e+ queue sizes after each generation")
     t_ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
     steps = sum(s1.steps) - sum(s0.steps)
     launches = s1.launches - s0.launches
@@ -268,7 +275,7 @@ def run_ours(a):
         traffic = NCU_BYTES_PER_STEP * steps / kern_n
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "kernel": "k_transport<float, species> x3 (one generation: e-, e+, gamma)",
+            "kernel": "k_transport<float, species> x3 (one launch = one generation: e-, e+, gamma)",
             "alg_bytes_per_launch": alg_bytes / kern_n if kern_n else None,
             "mean_launch_us": 1e3 * kern_ms / kern_n if kern_n else None,
             "launches": kern_n, "peak_kind": f"{peak_kind} (hbm_gbs burst copy)",
