@@ -150,8 +150,9 @@ typedef struct {
   uint64_t requests_done;
   uint64_t launches;      /* kernels launched by the library */
   uint64_t step_launches; /* generations timed (ADEPT_FLAG_TIME_STEPS) */
-  double step_kernel_ms;  /* summed CUDA-event durations of their three transport kernels */
-  double species_ms[3];   /* the same split by species kernel (gamma, e-, e+) */
+  double step_kernel_ms;  /* summed CUDA-event durations of their generations (fork to the
+                             end of the last of the three concurrent species kernels) */
+  double species_ms[3];   /* per species kernel (gamma, e-, e+): fork to its end, summed */
 } adept_stats;
 
 /* Create a context: validates geometry and materials, lays out dev_arena (device memory

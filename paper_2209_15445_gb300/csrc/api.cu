@@ -117,6 +117,8 @@ struct adept_ctx {
   cudaGraphExec_t graph = nullptr;
   int graph_gens = 0;
   std::vector<cudaEvent_t> ev;  // 4 per generation when timing: start, after e-, after e+, after gamma
+  cudaStream_t side[2] = {nullptr, nullptr};     // the e+ and gamma kernels run on these
+  cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
   // requests
   std::mutex mu;
   std::condition_variable cv;
@@ -337,6 +339,11 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     CK(cudaMemsetAsync(E.state, 0, sizeof(uint32_t) * ms, c->stream));
     CK(cudaHostAlloc(&c->h_ctrl, sizeof(Ctrl), cudaHostAllocDefault));
     CK(cudaHostAlloc(&c->h_done, sizeof(uint32_t) * kDoneChunk, cudaHostAllocDefault));
+    for (int j = 0; j < 2; ++j) {
+      CK(cudaStreamCreateWithFlags(&c->side[j], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&c->join[j], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     CK(cudaStreamSynchronize(c->stream));
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
@@ -541,16 +548,20 @@ static bool timing(const adept_ctx* c) { return (c->opt.flags & ADEPT_FLAG_TIME_
 // the generations of one chunk, optionally bracketed by timing events
 static cudaError_t enqueue_generations(adept_ctx* c, int gens) {
   cudaError_t e = cudaMemsetAsync(&c->P.ctrl->done_count, 0, sizeof(uint32_t), c->stream);
+  // fork e- (main stream), e+ and gamma (side streams), join, close: per generation
+  const unsigned rf = cudaEventRecordExternal;
   for (int k = 0; k < gens && e == cudaSuccess; ++k) {
-    // under stream capture an external record node makes the event fire when the graph runs
-    if (timing(c)) e = cudaEventRecordWithFlags(c->ev[4 * k], c->stream, cudaEventRecordExternal);
-    // e-, e+, then gamma: the gamma kernel closes the generation
-    int j = 1;
-    for (int sp : {1, 2, 0}) {
-      if (e == cudaSuccess) e = launch_transport(c->P, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, c->stream);
-      if (e == cudaSuccess && timing(c)) e = cudaEventRecordWithFlags(c->ev[4 * k + j], c->stream, cudaEventRecordExternal);
-      ++j;
+    e = cudaEventRecord(c->fork, c->stream);
+    if (e == cudaSuccess && timing(c)) e = cudaEventRecordWithFlags(c->ev[4 * k], c->stream, rf);
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->side[j], c->fork, 0);
+    cudaStream_t st[3] = {c->side[1], c->stream, c->side[0]};  // gamma, e-, e+
+    for (int sp : {0, 1, 2}) {
+      if (e == cudaSuccess) e = launch_transport(c->P, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, st[sp]);
+      if (e == cudaSuccess && timing(c)) e = cudaEventRecordWithFlags(c->ev[4 * k + 1 + sp], st[sp], rf);
     }
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventRecord(c->join[j], c->side[j]);
+    for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->stream, c->join[j], 0);
+    if (e == cudaSuccess) e = launch_close_generation(c->P, c->stream);
   }
   if (e == cudaSuccess) e = launch_finish(c->P, c->opt.precision, c->stream);
   return e;
@@ -587,19 +598,22 @@ static int run_chunk(adept_ctx* c) {
   } else {
     CK(enqueue_generations(c, 1));
   }
-  c->stats.launches += 3 * gens + 2;
+  c->stats.launches += 4 * gens + 2;
   CK(cudaMemcpyAsync(c->h_ctrl, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_done, c->P.evt.done_list, sizeof(uint32_t) * kDoneChunk, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (timing(c)) {
-    static const int order[3] = {1, 2, 0};
+    // concurrent species kernels: each one's time from the generation's fork to its end;
+    // the generation's time is the longest of the three
     for (int k = 0; k < gens; ++k) {
-      for (int j = 0; j < 3; ++j) {
+      float mx = 0.f;
+      for (int sp = 0; sp < 3; ++sp) {
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, c->ev[4 * k + j], c->ev[4 * k + j + 1]));
-        c->stats.step_kernel_ms += ms;
-        c->stats.species_ms[order[j]] += ms;
+        CK(cudaEventElapsedTime(&ms, c->ev[4 * k], c->ev[4 * k + 1 + sp]));
+        c->stats.species_ms[sp] += ms;
+        mx = ms > mx ? ms : mx;
       }
+      c->stats.step_kernel_ms += mx;
     }
     c->stats.step_launches += gens;
   }
@@ -907,6 +921,11 @@ extern "C" void adept_destroy(adept_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto e : c->ev) cudaEventDestroy(e);
+  for (int j = 0; j < 2; ++j) {
+    if (c->side[j]) { cudaStreamSynchronize(c->side[j]); cudaStreamDestroy(c->side[j]); }
+    if (c->join[j]) cudaEventDestroy(c->join[j]);
+  }
+  if (c->fork) cudaEventDestroy(c->fork);
   if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
   if (c->h_done) cudaFreeHost(c->h_done);
   if (c->h_stage) cudaFreeHost(c->h_stage);

@@ -543,8 +543,9 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
 
 // One generation of one species (paper Sec. 3: TransportElectrons, TransportPositrons and
 // TransportGammas). Persistent launch: each warp takes 32-track tiles of the current queue.
-// The three run back to back per generation (e-, e+, gamma); the last block of the gamma
-// kernel publishes the next queue sizes and advances the generation.
+// The three species kernels of a generation are independent (each reads its own current
+// queue and appends to the next ones atomically), so they run concurrently on three
+// streams; k_close_generation then publishes the next queue sizes.
 template <class R, int S, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
   __shared__ unsigned long long s_steps, s_created[3];
@@ -573,12 +574,16 @@ __global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
   if (s_steps) atomicAdd(&P.ctrl->steps[S], s_steps);
   for (int k = 0; k < 3; ++k)
     if (s_created[k]) atomicAdd(&P.ctrl->created[k], s_created[k]);
-  if (S != 0) return;
-  __threadfence();
-  const uint32_t ticket = atomicAdd(&P.ctrl->blocks_done, 1u);
-  if (ticket != gridDim.x - 1) return;
-  __threadfence();
+}
+
+// Close a generation once the three species kernels are done (they run concurrently):
+// publish the next queue sizes (clamped to the capacity; overflow was counted), log them,
+// empty the consumed queues and advance gen, whose parity selects the buffers.
+__global__ void k_close_generation(Params P) {
+  if (threadIdx.x != 0) return;
   volatile Ctrl* c = P.ctrl;
+  const uint32_t gen = c->gen;
+  const int p = gen & 1;
   uint32_t nn[3];
   for (int k = 0; k < 3; ++k) {
     uint32_t m = c->count[p ^ 1][k];
@@ -593,10 +598,13 @@ __global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
     c->log_n = ln + 1;
   }
   c->generations = c->generations + 1;
-  c->blocks_done = 0;
   __threadfence();
   c->gen = gen + 1;
-  __threadfence();
+}
+
+cudaError_t launch_close_generation(const Params& P, cudaStream_t st) {
+  k_close_generation<<<1, 32, 0, st>>>(P);
+  return cudaGetLastError();
 }
 
 // Each species kernel is compiled for 1..4 resident blocks of 256 threads per SM

@@ -121,9 +121,10 @@ cudaError_t launch_build_tables(const Params& P, const double* mat_in, int n_mat
                                 MatDev* mat, BuildScratch s, double2* g64, double2* e64, double2* p64,
                                 float2* g32, float2* e32, float2* p32, double* re64, double* rp64,
                                 float* re32, float* rp32, double* Tc, double* kc, cudaStream_t st);
-// one generation of one species; species 0 (gamma) must run last: it closes the generation
+// one generation of one species (the three may run concurrently), then the close
 cudaError_t launch_transport(const Params& P, int precision, int species, int minb, int grid, int block,
                              cudaStream_t st);
+cudaError_t launch_close_generation(const Params& P, cudaStream_t st);
 cudaError_t launch_admit(const Params& P, uint32_t slot_base, const uint32_t* keys, int n_slots,
                          cudaStream_t st);
 // meta: per track (event index within the request, track id)
