@@ -64,7 +64,7 @@ def args_parse():
     ap.add_argument("--events", type=int, default=10000)
     ap.add_argument("--energy", type=float, default=1e4)
     ap.add_argument("--precision", type=int, default=1)
-    ap.add_argument("--graph", type=int, default=32)
+    ap.add_argument("--graph", type=int, default=0, help="generations per CUDA graph (0 = tuned)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--arena-gb", type=float, default=10.0)
@@ -74,6 +74,8 @@ def args_parse():
                     help="c2 (default) is the headline line; the others are the configuration studies")
     ap.add_argument("--seconds", type=float, default=20.0, help="serving workload duration")
     ap.add_argument("--genlog", default="", help="write the per-generation queue sizes of the last step here")
+    ap.add_argument("--no-kernel-timing", action="store_true", help="no CUDA events around the transport kernels")
+    ap.add_argument("--species-timing", action="store_true", help="also time each species kernel")
     return ap.parse_args()
 
 
@@ -214,10 +216,17 @@ def run_ours(a):
     prim = W.electrons(n, E, first_event=rank * n)  # each rank: its own events
     host = A.tracks_array(prim)
     dev_tracks = torch.from_numpy(host.view(np.uint8).copy()).to(dev)
-    tr = A.Transport(geom, precision=a.precision, arena_bytes=int(a.arena_gb * (1 << 30)), graph_generations=a.graph,
-                     flags=A.FLAG_TIME_STEPS, max_events=max(65536, n), blocks_per_sm=a.bps,
-                     blocks_per_sm_species=(A.C.c_int32 * 3)(*([int(x) for x in a.bps_species.split(",")]
-                                                                if a.bps_species else [0, 0, 0])))
+    # launch settings: the autotuned ones (tuning.json) unless given on the command line
+    launch_opts = {}
+    if a.bps:
+        launch_opts["blocks_per_sm"] = a.bps
+    if a.bps_species:
+        launch_opts["blocks_per_sm_species"] = (A.C.c_int32 * 3)(*[int(x) for x in a.bps_species.split(",")])
+    if a.graph:
+        launch_opts["graph_generations"] = a.graph
+    tr = A.Transport(geom, precision=a.precision, arena_bytes=int(a.arena_gb * (1 << 30)),
+                     flags=0 if a.no_kernel_timing else (A.FLAG_TIME_SPECIES if a.species_timing else A.FLAG_TIME_STEPS),
+                     max_events=max(65536, n), **launch_opts)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB of L2
 
     def step_device():
@@ -275,12 +284,12 @@ def run_ours(a):
         traffic = NCU_BYTES_PER_STEP * steps / kern_n
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "kernel": "k_transport<float, species> x3 (one launch = one generation: e-, e+, gamma)",
+            "kernel": "k_transport<float, species> x3, concurrent (one launch = one generation: e-, e+, gamma)",
             "alg_bytes_per_launch": alg_bytes / kern_n if kern_n else None,
             "mean_launch_us": 1e3 * kern_ms / kern_n if kern_n else None,
             "launches": kern_n, "peak_kind": f"{peak_kind} (hbm_gbs burst copy)",
             "kernel_share_of_step_time": kern_ms / t_ms if t_ms else None,
-            "species_ms_per_step": [round(x / a.steps, 3) for x in species_ms]}
+            "species_ms_per_step": [round(x / a.steps, 3) for x in species_ms] if a.species_timing else None}
 
     # end to end through the C ABI with host buffers: submit copies host tracks to the device
     e2e = None
@@ -317,8 +326,9 @@ def run_ours(a):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32/f64" if a.precision else "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "events": n, "E_MeV": E, "precision": "split" if a.precision else "fp64",
-                           "graph_generations": a.graph, "block": tr.options.block_size or 256,
-                           "blocks_per_sm_variant": a.bps or (3 if a.precision else 2),
+                           "graph_generations": tr.options.graph_generations,
+                           "block": tr.options.block_size or 256,
+                           "blocks_per_sm_species": list(tr.options.blocks_per_sm_species) if not a.bps else [a.bps] * 3,
                            "l2": "track queues (GBs) exceed L2; 256 MB buffer written between steps"},
                 "showers_per_s": showers, "steps_per_shower": steps / (a.steps * n),
                 "energy_conserved": bool(edep_ok), "roofline": roof, "cpu_baseline": base, "e2e": e2e,
@@ -354,7 +364,7 @@ def run_study(a):
     if a.workload == "c1":
         # plain FP64, one event per transport, one generation per launch with the queue
         # sizes read back after each (the paper's small-batch form)
-        tr = A.Transport(W.slab_calorimeter(), precision=0, arena_bytes=1 << 30, graph_generations=0)
+        tr = A.Transport(W.slab_calorimeter(), precision=0, arena_bytes=1 << 30, graph_generations=-1)
         prim = W.electrons(100, 1000.0)
         arrs = [A.tracks_array(prim.take([i])) for i in range(100)]
         for k in range(a.warmup):
@@ -378,7 +388,7 @@ def run_study(a):
             name = "100,000 e-/gamma 1-50 GeV, |eta|<1.5, 20-layer barrel, 3.8 T; split, batched in 100 requests"
             chunks, arena = 100, 40 << 30
         tr = A.Transport(geom, precision=a.precision, field_T=field, arena_bytes=arena, graph_generations=a.graph,
-                         flags=A.FLAG_TIME_STEPS, max_events=200000, tracks_per_MeV=0.1)
+                         flags=A.FLAG_TIME_SPECIES, max_events=200000, tracks_per_MeV=0.1)
         n = len(prim)
         parts = [prim.take(np.arange(k * n // chunks, (k + 1) * n // chunks)) for k in range(chunks)]
         arrs = [A.tracks_array(pp) for pp in parts]

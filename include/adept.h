@@ -100,8 +100,8 @@ typedef struct {
   int32_t blocks_per_sm;      /* transport-kernel variant compiled for 1..4 resident
                                  256-thread blocks per SM (register cap 255/128/85/64); the
                                  persistent grid is SMs x its occupancy [3 split, 2 FP64] */
-  int32_t graph_generations;  /* generations per captured CUDA graph; 0 = launch each
-                                 generation and read the queue sizes after it [32] */
+  int32_t graph_generations;  /* generations per captured CUDA graph [32]; -1 = no graphs:
+                                 launch each generation and read the queue sizes after it */
   uint32_t seed;              /* Philox key word 0 [1] */
   uint32_t process_mask;      /* ADEPT_P_* bits, 0 = all [0] */
   uint32_t max_steps;         /* per-track step cap; the rest of the energy is "killed" [100000] */
@@ -114,9 +114,11 @@ typedef struct {
   int32_t blocks_per_sm_species[3]; /* per-species override of blocks_per_sm (gamma, e-, e+) [0] */
 } adept_options;
 
-/* adept_options.flags: time every step-kernel launch with CUDA events recorded around it
- * on the transport stream (inside the captured graphs); the totals appear in adept_stats */
+/* adept_options.flags: time every generation (its three transport kernels, from the fork to
+ * the join) with CUDA events recorded inside the captured graphs; totals in adept_stats */
 #define ADEPT_FLAG_TIME_STEPS 1
+/* also time each species kernel separately (two more events per generation) */
+#define ADEPT_FLAG_TIME_SPECIES 4
 
 /* One particle handed to the library. event is the caller's event number; it keys the
  * random streams together with the seed, so equal (seed, event, track order) inputs
@@ -149,10 +151,11 @@ typedef struct {
   uint64_t overflow;      /* tracks dropped for lack of capacity (transport then failed) */
   uint64_t requests_done;
   uint64_t launches;      /* kernels launched by the library */
-  uint64_t step_launches; /* generations timed (ADEPT_FLAG_TIME_STEPS) */
+  uint64_t step_launches; /* generations timed (ADEPT_FLAG_TIME_STEPS or _SPECIES) */
   double step_kernel_ms;  /* summed CUDA-event durations of their generations (fork to the
                              end of the last of the three concurrent species kernels) */
-  double species_ms[3];   /* per species kernel (gamma, e-, e+): fork to its end, summed */
+  double species_ms[3];   /* per species kernel (gamma, e-, e+): fork to its end, summed
+                             (ADEPT_FLAG_TIME_SPECIES only) */
 } adept_stats;
 
 /* Create a context: validates geometry and materials, lays out dev_arena (device memory

@@ -23,6 +23,7 @@ OK, EINVAL, ENOMEM, ESTATE, ECUDA, ETIMEOUT, EBUSY, ENOTFOUND = 0, -1, -2, -3, -
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ESTATE: "ESTATE", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT",
           EBUSY: "EBUSY", ENOTFOUND: "ENOTFOUND"}
 FLAG_TIME_STEPS = 1
+FLAG_TIME_SPECIES = 4
 P_COMPTON, P_CONVERSION, P_PHOTO, P_E_IONI, P_E_BREM, P_POS_IONI, P_POS_BREM, P_ANNIH = (1 << i for i in range(8))
 NNODE = 289
 
@@ -292,6 +293,16 @@ class Transport:
         cuts = adept_cuts(range_cut_mm, field_T, tracking_cut_MeV)
         o = adept_options()
         o.precision = precision
+        if opts.pop("tuned", True):
+            # launch settings found by paper_2209_15445_gb300.autotune for this geometry and
+            # precision, for the options the caller leaves unset
+            from . import autotune
+            t = autotune.load().get(autotune.key(geom.kind, precision))
+            if t:
+                opts.setdefault("graph_generations", t["graph_generations"])
+                opts.setdefault("block_size", t["block_size"])
+                if "blocks_per_sm" not in opts:
+                    opts.setdefault("blocks_per_sm_species", (C.c_int32 * 3)(*t["blocks_per_sm_species"]))
         for k, v in opts.items():
             setattr(o, k, v)
         self.options = o

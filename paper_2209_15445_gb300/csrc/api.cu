@@ -108,13 +108,16 @@ struct adept_ctx {
   size_t probe_bytes = 0;
   bool built = false;
   // host pinned buffers
-  Ctrl* h_ctrl = nullptr;
-  uint32_t* h_done = nullptr;
+  Ctrl* h_ctrl[2] = {nullptr, nullptr};     // status of the two chunks that may be in flight
+  uint32_t* h_done[2] = {nullptr, nullptr};
+  cudaEvent_t status_ev[2] = {nullptr, nullptr};
+  cudaEvent_t stage_ev = nullptr;            // the last copy out of the pinned staging buffer
+  cudaStream_t copy_stream = nullptr;        // result copies, overlapping the next chunk
   char* h_stage = nullptr;
   size_t h_stage_bytes = 0;
   // launch shape
   int grid[3] = {0, 0, 0}, block = 256, minb[3] = {1, 1, 1};  // per species
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per status buffer (own timing events)
   int graph_gens = 0;
   std::vector<cudaEvent_t> ev;  // 4 per generation when timing: start, after e-, after e+, after gamma
   cudaStream_t side[2] = {nullptr, nullptr};     // the e+ and gamma kernels run on these
@@ -254,10 +257,11 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (options) c->opt = *options;
   adept_options& o = c->opt;
   if (o.precision != 0 && o.precision != 1) return ADEPT_EINVAL;
-  if (o.flags & ~1) return ADEPT_EINVAL;
+  if (o.flags & ~5) return ADEPT_EINVAL;
   if (o.block_size == 0) o.block_size = 256;
   if (o.block_size < 32 || o.block_size > 256 || (o.block_size & 31)) return ADEPT_EINVAL;
-  if (o.graph_generations < 0 || o.graph_generations > 1024) return ADEPT_EINVAL;
+  if (o.graph_generations < -1 || o.graph_generations > 1024) return ADEPT_EINVAL;
+  if (o.graph_generations == 0) o.graph_generations = 32;
   if (o.seed == 0) o.seed = 1;
   if (o.max_steps == 0) o.max_steps = 100000;
   if (o.max_vacuum_steps == 0) o.max_vacuum_steps = 1000;
@@ -288,7 +292,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   const uint32_t ms = o.max_events;
   ok = ok && carve_n(cp, &E.key, ms) && carve_n(cp, &E.state, ms) && carve_n(cp, &E.alive, ms) &&
        carve_n(cp, &E.edep, (size_t)ms * c->n_bins) && carve_n(cp, &E.leaked, ms) && carve_n(cp, &E.killed, ms) &&
-       carve_n(cp, &E.done_list, ms);
+       carve_n(cp, &E.done_list[0], ms) && carve_n(cp, &E.done_list[1], ms);
   ok = ok && carve_n(cp, &P.gen_log, 3 * (size_t)o.max_generation_log);
   c->probe_bytes = (size_t)8 << 20;
   c->probe = static_cast<char*>(carve(cp, c->probe_bytes));
@@ -337,8 +341,13 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     CK(cudaMemcpyAsync(vb, c->vol_bin.data(), sizeof(int) * c->n_vol, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), c->stream));
     CK(cudaMemsetAsync(E.state, 0, sizeof(uint32_t) * ms, c->stream));
-    CK(cudaHostAlloc(&c->h_ctrl, sizeof(Ctrl), cudaHostAllocDefault));
-    CK(cudaHostAlloc(&c->h_done, sizeof(uint32_t) * kDoneChunk, cudaHostAllocDefault));
+    for (int b = 0; b < 2; ++b) {
+      CK(cudaHostAlloc(&c->h_ctrl[b], sizeof(Ctrl), cudaHostAllocDefault));
+      CK(cudaHostAlloc(&c->h_done[b], sizeof(uint32_t) * kDoneChunk, cudaHostAllocDefault));
+      CK(cudaEventCreateWithFlags(&c->status_ev[b], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
     for (int j = 0; j < 2; ++j) {
       CK(cudaStreamCreateWithFlags(&c->side[j], cudaStreamNonBlocking));
       CK(cudaEventCreateWithFlags(&c->join[j], cudaEventDisableTiming));
@@ -516,7 +525,7 @@ static int admit(adept_ctx* c) {
     const size_t mb = sizeof(uint32_t) * 2 * r->n, kb = sizeof(uint32_t) * nk;
     int rc = ensure_host_stage(c, tb + mb + kb + 64);
     if (rc) return rc;
-    CK(cudaStreamSynchronize(c->stream));  // the pinned buffer may still feed an earlier copy
+    CK(cudaEventSynchronize(c->stage_ev));  // the pinned buffer may still feed an earlier copy
     char* h = c->h_stage;
     if (tb) memcpy(h, r->host.data(), tb);
     memcpy(h + tb, r->meta.data(), mb);
@@ -526,6 +535,7 @@ static int admit(adept_ctx* c) {
     if (tb) CK(cudaMemcpyAsync(dst, h, tb, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->stage_meta + 2 * used, h + tb, mb, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->stage_keys, h + tb + mb, kb, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaEventRecord(c->stage_ev, c->stream));
     CK(launch_admit(c->P, r->slot_base, c->stage_keys, (int)nk, c->stream));
     CK(launch_init_primaries(c->P, src, c->stage_meta + 2 * used, (int)r->n, r->slot_base, c->opt.precision, c->stream));
     c->stats.launches += 2;
@@ -535,7 +545,7 @@ static int admit(adept_ctx* c) {
 
 // ---------------------------------------------------------------- generation chunks
 static int ensure_events(adept_ctx* c, int n) {
-  while ((int)c->ev.size() < 4 * n) {
+  while ((int)c->ev.size() < n) {
     cudaEvent_t a;
     CK(cudaEventCreate(&a));
     c->ev.push_back(a);
@@ -543,73 +553,93 @@ static int ensure_events(adept_ctx* c, int n) {
   return ADEPT_OK;
 }
 
-static bool timing(const adept_ctx* c) { return (c->opt.flags & ADEPT_FLAG_TIME_STEPS) != 0; }
+static bool timing(const adept_ctx* c) { return (c->opt.flags & (ADEPT_FLAG_TIME_STEPS | ADEPT_FLAG_TIME_SPECIES)) != 0; }
+static bool timing_species(const adept_ctx* c) { return (c->opt.flags & ADEPT_FLAG_TIME_SPECIES) != 0; }
 
-// the generations of one chunk, optionally bracketed by timing events
-static cudaError_t enqueue_generations(adept_ctx* c, int gens) {
-  cudaError_t e = cudaMemsetAsync(&c->P.ctrl->done_count, 0, sizeof(uint32_t), c->stream);
+// the generations of one chunk; timing events of status buffer b are ev[4 G b ...]
+static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b) {
+  cudaError_t e = cudaMemsetAsync(&c->P.ctrl->done_count[b], 0, sizeof(uint32_t), c->stream);
   // fork e- (main stream), e+ and gamma (side streams), join, close: per generation
   const unsigned rf = cudaEventRecordExternal;
+  cudaEvent_t* ev = c->ev.empty() ? nullptr : c->ev.data() + 4 * gens * b;
   for (int k = 0; k < gens && e == cudaSuccess; ++k) {
     e = cudaEventRecord(c->fork, c->stream);
-    if (e == cudaSuccess && timing(c)) e = cudaEventRecordWithFlags(c->ev[4 * k], c->stream, rf);
+    if (e == cudaSuccess && timing(c)) e = cudaEventRecordWithFlags(ev[4 * k], c->stream, rf);
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->side[j], c->fork, 0);
     cudaStream_t st[3] = {c->side[1], c->stream, c->side[0]};  // gamma, e-, e+
     for (int sp : {0, 1, 2}) {
       if (e == cudaSuccess) e = launch_transport(c->P, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, st[sp]);
-      if (e == cudaSuccess && timing(c)) e = cudaEventRecordWithFlags(c->ev[4 * k + 1 + sp], st[sp], rf);
+      if (e == cudaSuccess && timing_species(c)) e = cudaEventRecordWithFlags(ev[4 * k + 1 + sp], st[sp], rf);
     }
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventRecord(c->join[j], c->side[j]);
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->stream, c->join[j], 0);
+    // without the per-species split: one end event after the join
+    if (e == cudaSuccess && timing(c) && !timing_species(c)) e = cudaEventRecordWithFlags(ev[4 * k + 1], c->stream, rf);
     if (e == cudaSuccess) e = launch_close_generation(c->P, c->stream);
   }
-  if (e == cudaSuccess) e = launch_finish(c->P, c->opt.precision, c->stream);
+  if (e == cudaSuccess) e = launch_finish(c->P, b, c->stream);
   return e;
 }
 
-static int capture_graph(adept_ctx* c, int gens) {
+static int capture_graph(adept_ctx* c, int gens, int b) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = enqueue_generations(c, gens);
+  cudaError_t e = enqueue_generations(c, gens, b);
   cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
   if (e != cudaSuccess) return fail(c, ADEPT_ECUDA, "graph capture: %s", cudaGetErrorString(e));
   if (e2 != cudaSuccess) return fail(c, ADEPT_ECUDA, "graph capture end: %s", cudaGetErrorString(e2));
-  e = cudaGraphInstantiate(&c->graph, g, 0);
+  e = cudaGraphInstantiate(&c->graph[b], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(c, ADEPT_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
   c->graph_gens = gens;
   return ADEPT_OK;
 }
 
-// Run one chunk of generations, then read the control block and the done list.
-static int run_chunk(adept_ctx* c) {
+// Queue one chunk of generations and the copy of its status into buffer b; returns at once.
+static int launch_chunk(adept_ctx* c, int b) {
   const int G = c->opt.graph_generations;
   const int gens = G > 0 ? G : 1;
   if (timing(c)) {
-    int rc = ensure_events(c, gens);
+    int rc = ensure_events(c, 8 * gens);
     if (rc) return rc;
   }
   if (G > 0) {
-    if (!c->graph) {
-      int rc = capture_graph(c, G);
+    if (!c->graph[b]) {
+      int rc = capture_graph(c, G, b);
       if (rc) return rc;
     }
-    CK(cudaGraphLaunch(c->graph, c->stream));
+    CK(cudaGraphLaunch(c->graph[b], c->stream));
   } else {
-    CK(enqueue_generations(c, 1));
+    CK(enqueue_generations(c, 1, b));
   }
   c->stats.launches += 4 * gens + 2;
-  CK(cudaMemcpyAsync(c->h_ctrl, c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(c->h_done, c->P.evt.done_list, sizeof(uint32_t) * kDoneChunk, cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpyAsync(c->h_ctrl[b], c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(c->h_done[b], c->P.evt.done_list[b], sizeof(uint32_t) * kDoneChunk, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaEventRecord(c->status_ev[b], c->stream));
+  return ADEPT_OK;
+}
+
+// Wait for chunk b and account its timing events.
+static int wait_chunk(adept_ctx* c, int b) {
+  CK(cudaEventSynchronize(c->status_ev[b]));
   if (timing(c)) {
+    const int G = c->opt.graph_generations;
+    const int gens = G > 0 ? G : 1;
+    const cudaEvent_t* ev = c->ev.data() + 4 * gens * b;
     // concurrent species kernels: each one's time from the generation's fork to its end;
     // the generation's time is the longest of the three
     for (int k = 0; k < gens; ++k) {
+      if (!timing_species(c)) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ev[4 * k], ev[4 * k + 1]));
+        c->stats.step_kernel_ms += ms;
+        continue;
+      }
       float mx = 0.f;
       for (int sp = 0; sp < 3; ++sp) {
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, c->ev[4 * k], c->ev[4 * k + 1 + sp]));
+        CK(cudaEventElapsedTime(&ms, ev[4 * k], ev[4 * k + 1 + sp]));
         c->stats.species_ms[sp] += ms;
         mx = ms > mx ? ms : mx;
       }
@@ -621,20 +651,22 @@ static int run_chunk(adept_ctx* c) {
 }
 
 // copy a finished request's rows back and release its slots
-static int complete(adept_ctx* c, Request* r) {
+static int complete(adept_ctx* c, Request* r, int b) {
   const size_t nk = r->keys.size(), nb = c->n_bins;
   r->edep.resize(nk * nb);
   r->leaked.resize(nk);
   r->killed.resize(nk);
   if (nk) {
+    // the rows are final once chunk b has run; copy them while the next chunk computes
+    cudaStream_t cs = c->copy_stream;
+    CK(cudaStreamWaitEvent(cs, c->status_ev[b], 0));
     CK(cudaMemcpyAsync(r->edep.data(), c->P.evt.edep + (size_t)r->slot_base * nb, sizeof(double) * nk * nb,
-                       cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(r->leaked.data(), c->P.evt.leaked + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaMemcpyAsync(r->killed.data(), c->P.evt.killed + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaMemsetAsync(c->P.evt.state + r->slot_base, 0, sizeof(uint32_t) * nk, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+                       cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(r->leaked.data(), c->P.evt.leaked + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(r->killed.data(), c->P.evt.killed + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost, cs));
+    // a finished slot is never read again by the finish pass (state 2 or 0 are both inert)
+    CK(cudaMemsetAsync(c->P.evt.state + r->slot_base, 0, sizeof(uint32_t) * nk, cs));
+    CK(cudaStreamSynchronize(cs));
   }
   std::lock_guard<std::mutex> lk(c->mu);
   c->slots.release(r->slot_base, (uint32_t)nk);
@@ -651,30 +683,52 @@ static int complete(adept_ctx* c, Request* r) {
   return ADEPT_OK;
 }
 
+// The host keeps at most two chunks queued: while chunk b runs, chunk b^1 is already
+// behind it in the stream, so the GPU does not idle while the host reads b's status.
+// A speculative chunk that finds empty queues costs only empty launches.
 extern "C" int adept_transport(adept_ctx* c, uint64_t timeout_us) {
   if (!c) return ADEPT_EINVAL;
   if (!c->built) return fail(c, ADEPT_ESTATE, "adept_build_tables has not run");
   const auto t0 = Clock::now();
   std::vector<uint32_t> done;
   int idle_chunks = 0;
+  bool queued[2] = {false, false};
+  int b = 0;
+  int stop_rc = ADEPT_OK;  // set on timeout or overflow: launch nothing more, drain, return it
   for (;;) {
-    int rc = admit(c);
-    if (rc) return rc;
-    {
+    bool work = false;
+    if (stop_rc == ADEPT_OK) {
+      int rc = admit(c);
+      if (rc) return rc;
       std::lock_guard<std::mutex> lk(c->mu);
-      if (c->in_flight == 0 && c->pending.empty()) return ADEPT_OK;
+      work = c->in_flight > 0 || !c->pending.empty();
     }
-    rc = run_chunk(c);
+    if (work) {
+      for (int k : {b, b ^ 1}) {
+        if (!queued[k]) {
+          int rc = launch_chunk(c, k);
+          if (rc) return rc;
+          queued[k] = true;
+        }
+      }
+    }
+    if (!queued[b]) {
+      if (!queued[b ^ 1]) return stop_rc == ADEPT_OK ? ADEPT_OK : stop_rc;
+      b ^= 1;
+      continue;
+    }
+    int rc = wait_chunk(c, b);
     if (rc) return rc;
-    const Ctrl& h = *c->h_ctrl;
+    queued[b] = false;
+    const Ctrl& h = *c->h_ctrl[b];
     for (int k = 0; k < 3; ++k) { c->stats.steps[k] = h.steps[k]; c->stats.secondaries[k] = h.created[k]; }
     c->stats.generations = h.generations;
     c->stats.overflow = h.overflow;
-    const uint32_t nd = h.done_count;
-    done.assign(c->h_done, c->h_done + std::min(nd, kDoneChunk));
-    if (nd > kDoneChunk) {
+    const uint32_t nd = h.done_count[b];
+    done.assign(c->h_done[b], c->h_done[b] + std::min(nd, kDoneChunk));
+    if (nd > kDoneChunk) {  // list b is not rewritten before buffer b is queued again
       done.resize(nd);
-      CK(cudaMemcpy(done.data() + kDoneChunk, c->P.evt.done_list + kDoneChunk, sizeof(uint32_t) * (nd - kDoneChunk),
+      CK(cudaMemcpy(done.data() + kDoneChunk, c->P.evt.done_list[b] + kDoneChunk, sizeof(uint32_t) * (nd - kDoneChunk),
                     cudaMemcpyDeviceToHost));
     }
     for (uint32_t s : done) {
@@ -686,22 +740,25 @@ extern "C" int adept_transport(adept_ctx* c, uint64_t timeout_us) {
         r = it->second.get();
       }
       if (r->state == 1 && r->remaining > 0 && --r->remaining == 0) {
-        rc = complete(c, r);
+        rc = complete(c, r, b);
         if (rc) return rc;
       }
     }
     const uint32_t live = h.count[h.gen & 1][0] + h.count[h.gen & 1][1] + h.count[h.gen & 1][2];
     idle_chunks = (live == 0 && done.empty()) ? idle_chunks + 1 : 0;
-    if (idle_chunks > 4) {
+    if (idle_chunks > 8) {
       std::lock_guard<std::mutex> lk(c->mu);
       if (c->in_flight > 0) return fail(c, ADEPT_ESTATE, "requests in flight but no live tracks (internal error)");
     }
-    if (h.overflow) return fail(c, ADEPT_ENOMEM, "%llu tracks exceeded the queue capacity %u; results are incomplete",
-                                (unsigned long long)h.overflow, c->P.cap);
-    if (timeout_us) {
+    if (h.overflow && stop_rc == ADEPT_OK)
+      stop_rc = fail(c, ADEPT_ENOMEM, "%llu tracks exceeded the queue capacity %u; results are incomplete",
+                     (unsigned long long)h.overflow, c->P.cap);
+    if (timeout_us && stop_rc == ADEPT_OK) {
       const auto us = std::chrono::duration_cast<std::chrono::microseconds>(Clock::now() - t0).count();
-      if ((uint64_t)us >= timeout_us) return fail(c, ADEPT_ETIMEOUT, "transport stopped after %llu us", (unsigned long long)us);
+      if ((uint64_t)us >= timeout_us)
+        stop_rc = fail(c, ADEPT_ETIMEOUT, "transport stopped after %llu us", (unsigned long long)us);
     }
+    b ^= 1;
   }
 }
 
@@ -919,15 +976,21 @@ extern "C" const char* adept_last_error(const adept_ctx* c) { return c ? c->err.
 extern "C" void adept_destroy(adept_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (int b = 0; b < 2; ++b)
+    if (c->graph[b]) cudaGraphExecDestroy(c->graph[b]);
   for (auto e : c->ev) cudaEventDestroy(e);
   for (int j = 0; j < 2; ++j) {
     if (c->side[j]) { cudaStreamSynchronize(c->side[j]); cudaStreamDestroy(c->side[j]); }
     if (c->join[j]) cudaEventDestroy(c->join[j]);
   }
   if (c->fork) cudaEventDestroy(c->fork);
-  if (c->h_ctrl) cudaFreeHost(c->h_ctrl);
-  if (c->h_done) cudaFreeHost(c->h_done);
+  for (int b = 0; b < 2; ++b) {
+    if (c->h_ctrl[b]) cudaFreeHost(c->h_ctrl[b]);
+    if (c->h_done[b]) cudaFreeHost(c->h_done[b]);
+    if (c->status_ev[b]) cudaEventDestroy(c->status_ev[b]);
+  }
+  if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+  if (c->copy_stream) { cudaStreamSynchronize(c->copy_stream); cudaStreamDestroy(c->copy_stream); }
   if (c->h_stage) cudaFreeHost(c->h_stage);
   delete c;
 }

@@ -707,21 +707,20 @@ __global__ void k_mark(Params P) {
   }
 }
 
-__global__ void k_finish(Params P) {
+__global__ void k_finish(Params P, int b) {
   const uint32_t gen = __ldcg(&P.ctrl->gen);
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < P.evt.max_slots; s += gridDim.x * blockDim.x) {
     if (P.evt.state[s] == 1u && P.evt.alive[s] != gen) {
       P.evt.state[s] = 2u;
-      const uint32_t k = atomicAdd(&P.ctrl->done_count, 1u);
-      P.evt.done_list[k] = s;
+      const uint32_t k = atomicAdd(&P.ctrl->done_count[b], 1u);
+      P.evt.done_list[b][k] = s;
     }
   }
 }
 
-cudaError_t launch_finish(const Params& P, int precision, cudaStream_t st) {
-  (void)precision;
+cudaError_t launch_finish(const Params& P, int b, cudaStream_t st) {
   k_mark<<<1216, 256, 0, st>>>(P);
-  k_finish<<<(P.evt.max_slots + 255) / 256 < 1216 ? (P.evt.max_slots + 255) / 256 : 1216, 256, 0, st>>>(P);
+  k_finish<<<(P.evt.max_slots + 255) / 256 < 1216 ? (P.evt.max_slots + 255) / 256 : 1216, 256, 0, st>>>(P, b);
   return cudaGetLastError();
 }
 

@@ -65,10 +65,10 @@ struct Ctrl {
   uint32_t gen;               // generations run; parity gen & 1 holds the current queues
   uint32_t count[2][3];       // queue sizes [parity][species]
   uint32_t blocks_done;       // last-block detection in the step kernel
-  uint32_t done_count;        // events found finished by the last finish pass
+  uint32_t done_count[2];     // events found finished by the finish pass of a chunk (per buffer)
   uint32_t log_n;             // rows written to the generation log
   uint32_t error;             // first device-detected error code (0 = none)
-  uint32_t pad[5];
+  uint32_t pad[4];
   unsigned long long steps[3];
   unsigned long long created[3];
   unsigned long long overflow;
@@ -82,7 +82,7 @@ struct EventView {
   double* edep;        // [slot][n_bins]
   double* leaked;      // [slot]
   double* killed;      // [slot]
-  uint32_t* done_list; // slots found finished
+  uint32_t* done_list[2]; // slots found finished, one list per chunk buffer
   uint32_t max_slots;
 };
 
@@ -130,7 +130,7 @@ cudaError_t launch_admit(const Params& P, uint32_t slot_base, const uint32_t* ke
 // meta: per track (event index within the request, track id)
 cudaError_t launch_init_primaries(const Params& P, const TrackIn* recs, const uint32_t* meta, int n,
                                   uint32_t slot_base, int precision, cudaStream_t st);
-cudaError_t launch_finish(const Params& P, int precision, cudaStream_t st);
+cudaError_t launch_finish(const Params& P, int buffer, cudaStream_t st);
 cudaError_t launch_probe_philox(const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out,
                                 cudaStream_t st);
 cudaError_t launch_probe_interp(const Params& P, int s, int t, int m, int prec, const double* E, int n,
