@@ -119,6 +119,8 @@ typedef struct {
 #define ADEPT_FLAG_TIME_STEPS 1
 /* also time each species kernel separately (two more events per generation) */
 #define ADEPT_FLAG_TIME_SPECIES 4
+/* histogram the length of every step (validation; costs one atomic per step) */
+#define ADEPT_FLAG_STEP_HISTOGRAM 8
 
 /* One particle handed to the library. event is the caller's event number; it keys the
  * random streams together with the seed, so equal (seed, event, track order) inputs
@@ -210,6 +212,11 @@ int adept_get_stats(adept_ctx* ctx, adept_stats* out);
  * n_max rows of 3 uint32; returns the number of rows written (>= 0) or an error. */
 int adept_get_generation_log(adept_ctx* ctx, uint32_t* host_out, size_t n_max);
 int adept_reset_generation_log(adept_ctx* ctx);
+
+/* Step-length histogram since adept_init (ADEPT_FLAG_STEP_HISTOGRAM): 3 x 64 counts, species
+ * gamma, e-, e+, bin floor(log2(step / mm)) + 40 clamped to [0, 63]. The paper validates
+ * step-length distributions against Geant4 (Sec. 2.1). */
+int adept_get_step_histogram(adept_ctx* ctx, uint64_t* host_out);
 
 /* Production thresholds chosen for material m (MeV). */
 int adept_get_cuts(adept_ctx* ctx, int32_t m, double* e_cut, double* gamma_cut);

@@ -24,6 +24,7 @@ _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ESTATE: "ESTATE", ECUDA: "ECUDA", 
           EBUSY: "EBUSY", ENOTFOUND: "ENOTFOUND"}
 FLAG_TIME_STEPS = 1
 FLAG_TIME_SPECIES = 4
+FLAG_STEP_HISTOGRAM = 8
 P_COMPTON, P_CONVERSION, P_PHOTO, P_E_IONI, P_E_BREM, P_POS_IONI, P_POS_BREM, P_ANNIH = (1 << i for i in range(8))
 NNODE = 289
 
@@ -112,6 +113,7 @@ def load(path: str = LIB_PATH):
             "adept_get_generation_log": [vp, u32p, sz],
             "adept_reset_generation_log": [vp],
             "adept_get_cuts": [vp, i32, dp, dp],
+            "adept_get_step_histogram": [vp, C.POINTER(C.c_uint64)],
             "adept_get_table": [vp, i32, i32, i32, i32, dp],
             "adept_probe_philox": [vp, u32p, u32p, sz, u32p],
             "adept_probe_interp": [vp, i32, i32, i32, i32, dp, sz, dp],
@@ -205,6 +207,12 @@ def adept_get_generation_log(h, n_max=1 << 16):
     out = np.zeros((n_max, 3), np.uint32)
     n = load().adept_get_generation_log(h, _u32p(out), n_max)
     return n, out[: max(n, 0)]
+
+
+def adept_get_step_histogram(h):
+    out = np.zeros((3, 64), np.uint64)
+    rc = load().adept_get_step_histogram(h, out.ctypes.data_as(C.POINTER(C.c_uint64)))
+    return rc, out
 
 
 def adept_get_cuts(h, m):

@@ -134,6 +134,7 @@ struct adept_ctx {
   size_t in_flight = 0;
   adept_stats stats{};
   std::vector<uint32_t> gen_log_host;
+  unsigned long long* steplen = nullptr;  // device histogram (always carved, filled on request)
 };
 
 static int fail(adept_ctx* c, int code, const char* fmt, ...) {
@@ -257,7 +258,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (options) c->opt = *options;
   adept_options& o = c->opt;
   if (o.precision != 0 && o.precision != 1) return ADEPT_EINVAL;
-  if (o.flags & ~5) return ADEPT_EINVAL;
+  if (o.flags & ~13) return ADEPT_EINVAL;
   if (o.block_size == 0) o.block_size = 256;
   if (o.block_size < 32 || o.block_size > 256 || (o.block_size & 31)) return ADEPT_EINVAL;
   if (o.graph_generations < -1 || o.graph_generations > 1024) return ADEPT_EINVAL;
@@ -294,6 +295,8 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
        carve_n(cp, &E.edep, (size_t)ms * c->n_bins) && carve_n(cp, &E.leaked, ms) && carve_n(cp, &E.killed, ms) &&
        carve_n(cp, &E.done_list[0], ms) && carve_n(cp, &E.done_list[1], ms);
   ok = ok && carve_n(cp, &P.gen_log, 3 * (size_t)o.max_generation_log);
+  unsigned long long* steplen = nullptr;
+  ok = ok && carve_n(cp, &steplen, 3 * 64);
   c->probe_bytes = (size_t)8 << 20;
   c->probe = static_cast<char*>(carve(cp, c->probe_bytes));
   ok = ok && c->probe;
@@ -332,6 +335,8 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   P.field_T = cuts->field_T;
   P.tcut = cuts->tracking_cut_MeV;
   P.seed = o.seed; P.process_mask = o.process_mask; P.max_steps = o.max_steps; P.max_vac = o.max_vacuum_steps;
+  P.steplen = (o.flags & ADEPT_FLAG_STEP_HISTOGRAM) ? steplen : nullptr;
+  c->steplen = steplen;
   // device state
   adept_ctx* c_ = cp;
   {
@@ -340,6 +345,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     CK(cudaMemcpyAsync(vm, c->vol_mat.data(), sizeof(int) * c->n_vol, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(vb, c->vol_bin.data(), sizeof(int) * c->n_vol, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), c->stream));
+    CK(cudaMemsetAsync(steplen, 0, sizeof(unsigned long long) * 3 * 64, c->stream));
     CK(cudaMemsetAsync(E.state, 0, sizeof(uint32_t) * ms, c->stream));
     for (int b = 0; b < 2; ++b) {
       CK(cudaHostAlloc(&c->h_ctrl[b], sizeof(Ctrl), cudaHostAllocDefault));
@@ -835,6 +841,13 @@ extern "C" int adept_get_generation_log(adept_ctx* c, uint32_t* host_out, size_t
 extern "C" int adept_reset_generation_log(adept_ctx* c) {
   if (!c) return ADEPT_EINVAL;
   CK(cudaMemsetAsync(&c->P.ctrl->log_n, 0, sizeof(uint32_t), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ADEPT_OK;
+}
+
+extern "C" int adept_get_step_histogram(adept_ctx* c, uint64_t* host_out) {
+  if (!c || !host_out) return ADEPT_EINVAL;
+  CK(cudaMemcpyAsync(host_out, c->steplen, sizeof(uint64_t) * 3 * 64, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return ADEPT_OK;
 }

@@ -337,6 +337,12 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
   }
   if (boundary && P.geo.kind == 0 && next >= 0) t.z = __ldg(P.geo.bnd + (t.u[2] > (R)0 ? vol + 1 : vol));
   t.step = step + 1;
+  if (P.steplen && s > (R)0 && s < M<R>::big()) {
+    // validation histogram of step lengths: bin = floor(log2 s[mm]) + 40
+    int b = ilogb(s) + 40;
+    b = b < 0 ? 0 : (b > 63 ? 63 : b);
+    atomicAdd(P.steplen + 64 * S + b, 1ull);
+  }
 
   // S7: continuous loss by inverting the range table
   if (q != 0 && m >= 0) {

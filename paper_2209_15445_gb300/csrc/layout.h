@@ -99,6 +99,7 @@ struct Params {
   double field_T;
   double tcut;
   uint32_t seed, process_mask, max_steps, max_vac;
+  unsigned long long* steplen;  // [3][64] step-length histogram (log2 bins), or null
 };
 
 // device view of one submitted particle; same layout as adept_track in adept.h

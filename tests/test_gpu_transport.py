@@ -230,3 +230,37 @@ def test_alone_equals_in_mix():
     mixed, _ = tr.result(ra, 1)
     np.testing.assert_allclose(mixed, alone, rtol=1e-9, atol=1e-9)
     tr.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_secondary_counts_and_step_lengths(precision):
+    """Secondaries per species and the step-length distribution per species against the
+    oracle (the paper compares secondary counts "to the per-mil level", Sec. 2.2, and
+    validates step-length distributions, Sec. 2.1): identical in FP64, within 1 per mil
+    (counts) and a chi-square test (histograms) in the split form."""
+    need_gpu()
+    from paper_2209_15445_gb300 import adept as A
+    from scipy import stats
+    geom = W.slab_calorimeter()
+    prim = W.electrons(1000, 1e4)
+    tr = make(geom, precision=precision, arena_bytes=4 << 30, flags=A.FLAG_STEP_HISTOGRAM)
+    gpu_run(tr, prim)
+    st = tr.stats()
+    rc, hist = A.adept_get_step_histogram(tr.h)
+    assert rc == 0
+    tr.close()
+    ref = oracle.Oracle(geom).transport(prim, steplen=True)
+    g_sec = np.array(list(st.secondaries), np.int64)
+    o_sec = ref["created"].astype(np.int64)
+    g_steps = np.array(list(st.steps), np.int64)
+    if precision == 0:
+        np.testing.assert_array_equal(g_sec, o_sec)
+        np.testing.assert_array_equal(g_steps, ref["steps"].astype(np.int64))
+        np.testing.assert_array_equal(hist.astype(np.int64), ref["steplen"].astype(np.int64))
+    else:
+        assert np.all(np.abs(g_sec - o_sec) <= 1e-3 * o_sec), (g_sec, o_sec)
+        for sp in range(3):
+            a, b = hist[sp].astype(float), ref["steplen"][sp].astype(float)
+            keep = (a + b) > 50
+            chi2 = np.sum((a[keep] - b[keep]) ** 2 / (a[keep] + b[keep]))
+            assert stats.chi2.sf(chi2, keep.sum()) > 1e-4, (sp, chi2, keep.sum())
