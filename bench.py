@@ -189,6 +189,20 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def reduce_over_ranks(t, steps, device):
+    """Whole-job timing over replicas: the slowest rank's time and the sum of all ranks'
+    tracked steps (device None: a single process)."""
+    if device is None:
+        return t, steps
+    import torch
+    import torch.distributed as dist
+    v = torch.tensor([float(t), float(steps)], dtype=torch.float64, device=device)
+    vmax = v.clone()
+    dist.all_reduce(vmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    return float(vmax[0]), int(v[1])
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -262,15 +276,7 @@ def run_ours(a):
     kern_n = s1.step_launches - s0.step_launches
     species_ms = [s1.species_ms[k] - s0.species_ms[k] for k in range(3)]
     edep_ok = abs(meta.deposited_MeV + meta.leaked_MeV + meta.killed_MeV - n * E) <= 1e-9 * n * E
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_ms, float(steps), kern_ms, float(kern_n)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        t_ms_max, steps_all = float(tmax[0]), int(t[1])
-    else:
-        t_ms_max, steps_all = t_ms, steps
+    t_ms_max, steps_all = reduce_over_ranks(t_ms, steps, dev if ws > 1 else None)
     value = steps_all / (t_ms_max / 1e3)
     showers = ws * n * a.steps / (t_ms_max / 1e3)
 
@@ -306,13 +312,7 @@ def run_ours(a):
         e1 = tr.stats()
         k2 = max(1, a.steps // 2)
         st2 = sum(e1.steps) - sum(e0.steps)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([dt, float(st2)], dtype=torch.float64, device=dev)
-            tm = t.clone()
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-            dist.all_reduce(t, op=dist.ReduceOp.SUM)
-            dt, st2 = float(tm[0]), int(t[1])
+        dt, st2 = reduce_over_ranks(dt, st2, dev if ws > 1 else None)
         e2e = {"value": st2 / dt, "unit": UNIT, "h2d_bytes_per_step": int(n * (72 + 8) + 4 * n),
                "d2h_bytes_per_step": int(n * (geom.n_bins + 2) * 8), "steps": k2,
                "showers_per_s": ws * n * k2 / dt}
