@@ -232,13 +232,12 @@ static size_t track_bytes(int precision) {
 }
 
 static bool carve_queue(adept_ctx* c, TrackSoA* q, uint32_t cap) {
-  const size_t du = c->opt.precision ? 4 : 8;
-  bool ok = carve_n(c, &q->x, cap) && carve_n(c, &q->y, cap) && carve_n(c, &q->z, cap);
-  q->ux = carve(c, du * cap); q->uy = carve(c, du * cap); q->uz = carve(c, du * cap);
-  ok = ok && q->ux && q->uy && q->uz;
-  ok = ok && carve_n(c, &q->E, cap) && carve_n(c, &q->id, cap) && carve_n(c, &q->ev, cap) &&
-       carve_n(c, &q->step, cap) && carve_n(c, &q->nav, cap);
-  return ok;
+  *q = TrackSoA{};
+  if (c->opt.precision)  // split form: four arrays of 16-byte vectors
+    return carve_n(c, &q->xy, cap) && carve_n(c, &q->zE, cap) && carve_n(c, &q->un, cap) && carve_n(c, &q->meta, cap);
+  return carve_n(c, &q->x, cap) && carve_n(c, &q->y, cap) && carve_n(c, &q->z, cap) && carve_n(c, &q->ux, cap) &&
+         carve_n(c, &q->uy, cap) && carve_n(c, &q->uz, cap) && carve_n(c, &q->E, cap) && carve_n(c, &q->id, cap) &&
+         carve_n(c, &q->ev, cap) && carve_n(c, &q->step, cap) && carve_n(c, &q->nav, cap);
 }
 
 extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const adept_material* materials,

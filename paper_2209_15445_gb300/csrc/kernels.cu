@@ -205,31 +205,54 @@ template <class R> struct Trk {
 };
 
 template <class R>
-__device__ __forceinline__ void load_track(const TrackSoA& q, uint32_t i, Trk<R>& t) {
+__device__ __forceinline__ void load_track(const TrackSoA& q, uint32_t i, Trk<R>& t);
+template <>
+__device__ __forceinline__ void load_track<double>(const TrackSoA& q, uint32_t i, Trk<double>& t) {
   t.x = q.x[i]; t.y = q.y[i]; t.z = q.z[i];
-  t.u[0] = static_cast<const R*>(q.ux)[i];
-  t.u[1] = static_cast<const R*>(q.uy)[i];
-  t.u[2] = static_cast<const R*>(q.uz)[i];
+  t.u[0] = q.ux[i]; t.u[1] = q.uy[i]; t.u[2] = q.uz[i];
   t.E = q.E[i];
   t.id = q.id[i];
   t.ev = q.ev[i];
   t.step = q.step[i];
   t.nav = q.nav[i];
 }
+template <>
+__device__ __forceinline__ void load_track<float>(const TrackSoA& q, uint32_t i, Trk<float>& t) {
+  const double2 a = __ldcs(q.xy + i), b = __ldcs(q.zE + i);
+  const float4 c = __ldcs(q.un + i);
+  const uint4 d = __ldcs(q.meta + i);
+  t.x = a.x; t.y = a.y; t.z = b.x; t.E = b.y;
+  t.u[0] = c.x; t.u[1] = c.y; t.u[2] = c.z;
+  t.nav = __float_as_uint(c.w);
+  t.id = (unsigned long long)d.x | ((unsigned long long)d.y << 32);
+  t.ev = d.z;
+  t.step = d.w;
+}
 
 template <class R>
 __device__ __forceinline__ void store_track(const TrackSoA& q, uint32_t i, double x, double y, double z, R ux,
                                             R uy, R uz, double E, unsigned long long id, uint32_t ev,
-                                            uint32_t step, uint32_t nav) {
+                                            uint32_t step, uint32_t nav);
+template <>
+__device__ __forceinline__ void store_track<double>(const TrackSoA& q, uint32_t i, double x, double y, double z,
+                                                    double ux, double uy, double uz, double E, unsigned long long id,
+                                                    uint32_t ev, uint32_t step, uint32_t nav) {
   q.x[i] = x; q.y[i] = y; q.z[i] = z;
-  static_cast<R*>(q.ux)[i] = ux;
-  static_cast<R*>(q.uy)[i] = uy;
-  static_cast<R*>(q.uz)[i] = uz;
+  q.ux[i] = ux; q.uy[i] = uy; q.uz[i] = uz;
   q.E[i] = E;
   q.id[i] = id;
   q.ev[i] = ev;
   q.step[i] = step;
   q.nav[i] = nav;
+}
+template <>
+__device__ __forceinline__ void store_track<float>(const TrackSoA& q, uint32_t i, double x, double y, double z,
+                                                   float ux, float uy, float uz, double E, unsigned long long id,
+                                                   uint32_t ev, uint32_t step, uint32_t nav) {
+  q.xy[i] = make_double2(x, y);
+  q.zE[i] = make_double2(z, E);
+  q.un[i] = make_float4(ux, uy, uz, __uint_as_float(nav));
+  q.meta[i] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), ev, step);
 }
 
 template <class R> __device__ __forceinline__ const typename Pair2<R>::T* tab_g(const TableView& T);
@@ -708,7 +731,8 @@ __global__ void k_mark(Params P) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int sp = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);
     const uint32_t j = sp == 0 ? i : (sp == 1 ? i - n0 : i - n0 - n1);
-    const uint32_t ev = P.q[p][sp].ev[j];
+    const TrackSoA& q = P.q[p][sp];
+    const uint32_t ev = q.meta ? q.meta[j].z : q.ev[j];
     if (P.evt.alive[ev] != gen) P.evt.alive[ev] = gen;
   }
 }

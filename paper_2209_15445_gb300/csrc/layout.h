@@ -46,16 +46,23 @@ struct TableView {
   const double* Tc; const double* kc;
 };
 
-// One species' queue in structure-of-arrays form. Directions are double (plain form)
-// or float (split form) and addressed through void pointers of the chosen width.
+// One species' queue. Plain form: one array per field. Split form: the 64-byte track in
+// four arrays of 16-byte vectors (x,y | z,E | ux,uy,uz,nav | id lo,id hi,event,step), so
+// that a warp moves a track with four coalesced 128-bit loads and stores.
 struct TrackSoA {
+  // plain form
   double *x, *y, *z;
-  void *ux, *uy, *uz;
+  double *ux, *uy, *uz;
   double* E;
   unsigned long long* id;
   uint32_t* ev;    // event slot
   uint32_t* step;  // steps taken by this track
   uint32_t* nav;   // volume (low 16 bits) | consecutive vacuum steps (high 16 bits)
+  // split form
+  double2* xy;
+  double2* zE;
+  float4* un;      // direction and nav (bits)
+  uint4* meta;     // id lo, id hi, event slot, step
 };
 
 // Device control block: queue sizes for the two buffer parities, generation counter,
