@@ -49,7 +49,7 @@ NCU_SRC_HASH = "b09af856d4b60efd"
 
 def kernel_src_hash() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "device.cuh", "layout.h"):
+    for f in ("kernels.cu", "fused.cu", "transport.cuh", "device.cuh", "layout.h"):
         with open(os.path.join(ROOT, "paper_2209_15445_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -76,6 +76,8 @@ def args_parse():
     ap.add_argument("--genlog", default="", help="write the per-generation queue sizes of the last step here")
     ap.add_argument("--no-kernel-timing", action="store_true", help="no CUDA events around the transport kernels")
     ap.add_argument("--species-timing", action="store_true", help="also time each species kernel")
+    ap.add_argument("--fused", type=int, default=-1, choices=[-1, 0, 1],
+                    help="1: one kernel per generation for all species; 0: concurrent species kernels; -1: tuned")
     return ap.parse_args()
 
 
@@ -238,6 +240,8 @@ def run_ours(a):
         launch_opts["blocks_per_sm_species"] = (A.C.c_int32 * 3)(*[int(x) for x in a.bps_species.split(",")])
     if a.graph:
         launch_opts["graph_generations"] = a.graph
+    if a.fused >= 0:
+        launch_opts["fused"] = a.fused
     tr = A.Transport(geom, precision=a.precision, arena_bytes=int(a.arena_gb * (1 << 30)),
                      flags=0 if a.no_kernel_timing else (A.FLAG_TIME_SPECIES if a.species_timing else A.FLAG_TIME_STEPS),
                      max_events=max(65536, n), **launch_opts)
@@ -290,7 +294,9 @@ def run_ours(a):
         traffic = NCU_BYTES_PER_STEP * steps / kern_n
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "kernel": "k_transport<float, species> x3, concurrent (one launch = one generation: e-, e+, gamma)",
+            "kernel": ("k_fused_generation<%s> (one launch = one generation, all species)" if tr.options.fused else
+                       "k_transport<%s, species> x3, concurrent (one launch = one generation: e-, e+, gamma)")
+                      % ("float" if a.precision else "double"),
             "alg_bytes_per_launch": alg_bytes / kern_n if kern_n else None,
             "mean_launch_us": 1e3 * kern_ms / kern_n if kern_n else None,
             "launches": kern_n, "peak_kind": f"{peak_kind} (hbm_gbs burst copy)",
@@ -328,6 +334,8 @@ def run_ours(a):
                 "config": {"workload": WORKLOAD, "events": n, "E_MeV": E, "precision": "split" if a.precision else "fp64",
                            "graph_generations": tr.options.graph_generations,
                            "block": tr.options.block_size or 256,
+                           "fused": int(tr.options.fused),
+                           "blocks_per_sm": int(tr.options.blocks_per_sm),
                            "blocks_per_sm_species": list(tr.options.blocks_per_sm_species) if not a.bps else [a.bps] * 3,
                            "l2": "track queues (GBs) exceed L2; 256 MB buffer written between steps"},
                 "showers_per_s": showers, "steps_per_shower": steps / (a.steps * n),
@@ -387,8 +395,10 @@ def run_study(a):
             geom, field, prim = W.barrel_calorimeter(), 3.8, W.barrel_primaries(100000, seed=4)
             name = "100,000 e-/gamma 1-50 GeV, |eta|<1.5, 20-layer barrel, 3.8 T; split, batched in 100 requests"
             chunks, arena = 100, 40 << 30
+        fo = {"fused": a.fused} if a.fused >= 0 else {}
         tr = A.Transport(geom, precision=a.precision, field_T=field, arena_bytes=arena, graph_generations=a.graph,
-                         flags=A.FLAG_TIME_SPECIES, max_events=200000, tracks_per_MeV=0.1)
+                         flags=A.FLAG_TIME_STEPS if a.fused == 1 else A.FLAG_TIME_SPECIES, max_events=200000,
+                         tracks_per_MeV=0.1, **fo)
         n = len(prim)
         parts = [prim.take(np.arange(k * n // chunks, (k + 1) * n // chunks)) for k in range(chunks)]
         arrs = [A.tracks_array(pp) for pp in parts]
@@ -411,8 +421,11 @@ def run_study(a):
         return
     # c5: serving -- 16 producers in a closed loop, one driver thread running the transport
     geom = W.barrel_calorimeter()
+    # serving keeps few tracks per generation in flight: one fused kernel per generation
+    # (less launch latency per generation) serves it faster than concurrent species kernels
+    fo = {"fused": a.fused if a.fused >= 0 else 1}
     tr = A.Transport(geom, precision=a.precision, field_T=3.8, arena_bytes=24 << 30, graph_generations=8,
-                     max_events=65536, tracks_per_MeV=0.1)
+                     max_events=65536, tracks_per_MeV=0.1, **fo)
     stop = threading.Event()
     lat, done_steps, errors = [], [0], []
     lock = threading.Lock()

@@ -112,6 +112,10 @@ typedef struct {
   double tracks_per_MeV;      /* admission estimate of peak live tracks per MeV [0.25] */
   int32_t flags;              /* ADEPT_FLAG_* bits [0] */
   int32_t blocks_per_sm_species[3]; /* per-species override of blocks_per_sm (gamma, e-, e+) [0] */
+  int32_t fused;              /* 0: per generation, three species kernels run concurrently
+                                 and a close kernel follows them; 1: one kernel per generation
+                                 for all three species, whose last block closes the generation;
+                                 blocks_per_sm picks its variant (2 or 3 split, 1 or 2 FP64) [0] */
 } adept_options;
 
 /* adept_options.flags: time every generation (its three transport kernels, from the fork to
@@ -155,7 +159,8 @@ typedef struct {
   uint64_t launches;      /* kernels launched by the library */
   uint64_t step_launches; /* generations timed (ADEPT_FLAG_TIME_STEPS or _SPECIES) */
   double step_kernel_ms;  /* summed CUDA-event durations of their generations (fork to the
-                             end of the last of the three concurrent species kernels) */
+                             end of the last of the three concurrent species kernels, or the
+                             fused kernel) */
   double species_ms[3];   /* per species kernel (gamma, e-, e+): fork to its end, summed
                              (ADEPT_FLAG_TIME_SPECIES only) */
 } adept_stats;

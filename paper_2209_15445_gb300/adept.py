@@ -56,7 +56,7 @@ class adept_options(C.Structure):
                 ("max_steps", C.c_uint32), ("max_vacuum_steps", C.c_uint32), ("max_events", C.c_uint32),
                 ("max_generation_log", C.c_uint32), ("track_capacity", C.c_uint64),
                 ("tracks_per_MeV", C.c_double), ("flags", C.c_int32),
-                ("blocks_per_sm_species", C.c_int32 * 3)]
+                ("blocks_per_sm_species", C.c_int32 * 3), ("fused", C.c_int32)]
 
 
 TRACK_DTYPE = np.dtype([("pdg", "<i4"), ("pad0", "<i4"), ("E", "<f8"), ("pos", "<f8", 3), ("dir", "<f8", 3),
@@ -309,7 +309,10 @@ class Transport:
             if t:
                 opts.setdefault("graph_generations", t["graph_generations"])
                 opts.setdefault("block_size", t["block_size"])
-                if "blocks_per_sm" not in opts:
+                opts.setdefault("fused", t.get("fused", 0))
+                if opts["fused"] and t.get("fused"):
+                    opts.setdefault("blocks_per_sm", t["blocks_per_sm"])
+                elif "blocks_per_sm" not in opts and "blocks_per_sm_species" in t:
                     opts.setdefault("blocks_per_sm_species", (C.c_int32 * 3)(*t["blocks_per_sm_species"]))
         for k, v in opts.items():
             setattr(o, k, v)

@@ -4,7 +4,7 @@ Measures tracked steps/s of a workload on the current GPU for candidate launch s
 and keeps the fastest: the CUDA-graph chunk length, the block size, and per species the
 register-cap variant of its transport kernel (how many 256-thread blocks per SM it is
 compiled for, which trades occupancy against spills). Search: coordinate descent from
-the library defaults. The result is written to tuning.json next to this file, keyed by
+the library defaults, then the fused one-kernel-per-generation mode with its variants. The result is written to tuning.json next to this file, keyed by
 "<geometry kind>/<precision>", and `adept.Transport` applies it to options the caller
 leaves at zero.
 
@@ -42,10 +42,11 @@ def measure(geom, prim, precision, field_T, cfg, repeat=2):
     from . import adept as A
 
     bps = cfg.get("blocks_per_sm_species", [0, 0, 0])
+    extra = {"fused": 1, "blocks_per_sm": cfg["blocks_per_sm"]} if cfg.get("fused") else \
+        {"blocks_per_sm_species": (A.C.c_int32 * 3)(*bps)}
     tr = A.Transport(geom, precision=precision, field_T=field_T, arena_bytes=cfg.get("arena_bytes", 10 << 30),
                      graph_generations=cfg["graph_generations"], block_size=cfg["block_size"],
-                     blocks_per_sm_species=(A.C.c_int32 * 3)(*bps), max_events=max(65536, len(prim)),
-                     tuned=False)
+                     max_events=max(65536, len(prim)), tuned=False, **extra)
     arr = A.tracks_array(prim)
     n_ev = len(np.unique(prim.event))
     rid = tr.submit(arr); tr.transport(); tr.result(rid, n_ev)  # warm-up (graph capture)
@@ -86,6 +87,18 @@ def tune(geom, prim, precision, field_T=0.0, log=print):
             log(f"  {what}={v}: failed ({e})")
             continue
         log(f"  {what}={v}: {r:.3e}")
+        if r > best * 1.005:
+            best, cfg = r, c
+    # the fused mode: one kernel per generation, one register-cap variant for all species
+    for v in ((2, 3) if precision else (1, 2)):
+        c = dict(cfg, fused=1, blocks_per_sm=v)
+        c.pop("blocks_per_sm_species", None)
+        try:
+            r = measure(geom, prim, precision, field_T, c)
+        except Exception as e:
+            log(f"  fused blocks_per_sm={v}: failed ({e})")
+            continue
+        log(f"  fused blocks_per_sm={v}: {r:.3e}")
         if r > best * 1.005:
             best, cfg = r, c
     cfg["steps_per_s"] = best

@@ -117,11 +117,16 @@ struct adept_ctx {
   size_t h_stage_bytes = 0;
   // launch shape
   int grid[3] = {0, 0, 0}, block = 256, minb[3] = {1, 1, 1};  // per species
+  int fgrid = 0, fminb = 0;  // fused generation kernel
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per status buffer (own timing events)
   int graph_gens = 0;
   std::vector<cudaEvent_t> ev;  // 4 per generation when timing: start, after e-, after e+, after gamma
   cudaStream_t side[2] = {nullptr, nullptr};     // the e+ and gamma kernels run on these
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+  // timing: the event-record nodes hang off the generation chain on their own stream, so
+  // that nothing on the chain waits for them (kdone[sp]: species sp's kernel has ended)
+  cudaStream_t tstream = nullptr;
+  cudaEvent_t kdone[3] = {nullptr, nullptr, nullptr}, tjoin = nullptr;
   // requests
   std::mutex mu;
   std::condition_variable cv;
@@ -257,7 +262,9 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (options) c->opt = *options;
   adept_options& o = c->opt;
   if (o.precision != 0 && o.precision != 1) return ADEPT_EINVAL;
-  if (o.flags & ~13) return ADEPT_EINVAL;
+  if (o.flags & ~(ADEPT_FLAG_TIME_STEPS | ADEPT_FLAG_TIME_SPECIES | ADEPT_FLAG_STEP_HISTOGRAM)) return ADEPT_EINVAL;
+  if (o.fused != 0 && o.fused != 1) return ADEPT_EINVAL;
+  if (o.fused && (o.flags & ADEPT_FLAG_TIME_SPECIES)) return ADEPT_EINVAL;  // needs separate species kernels
   if (o.block_size == 0) o.block_size = 256;
   if (o.block_size < 32 || o.block_size > 256 || (o.block_size & 31)) return ADEPT_EINVAL;
   if (o.graph_generations < -1 || o.graph_generations > 1024) return ADEPT_EINVAL;
@@ -296,6 +303,8 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   ok = ok && carve_n(cp, &P.gen_log, 3 * (size_t)o.max_generation_log);
   unsigned long long* steplen = nullptr;
   ok = ok && carve_n(cp, &steplen, 3 * 64);
+  TrackSoA* qdesc = nullptr;
+  ok = ok && carve_n(cp, &qdesc, 6);
   c->probe_bytes = (size_t)8 << 20;
   c->probe = static_cast<char*>(carve(cp, c->probe_bytes));
   ok = ok && c->probe;
@@ -323,6 +332,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     for (int s = 0; s < 3; ++s)
       if (!carve_queue(cp, &P.q[par][s], (uint32_t)cap)) return ADEPT_ENOMEM;
   P.cap = (uint32_t)cap;
+  P.qd = qdesc;
   // views
   P.geo.kind = c->kind; P.geo.n_vol = c->n_vol; P.geo.n_bins = c->n_bins;
   P.geo.half_xy = geometry->transverse_half_mm; P.geo.half_z = geometry->half_length_mm;
@@ -344,6 +354,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     CK(cudaMemcpyAsync(vm, c->vol_mat.data(), sizeof(int) * c->n_vol, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(vb, c->vol_bin.data(), sizeof(int) * c->n_vol, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(P.ctrl, 0, sizeof(Ctrl), c->stream));
+    CK(cudaMemcpyAsync(qdesc, &P.q[0][0], sizeof(TrackSoA) * 6, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(steplen, 0, sizeof(unsigned long long) * 3 * 64, c->stream));
     CK(cudaMemsetAsync(E.state, 0, sizeof(uint32_t) * ms, c->stream));
     for (int b = 0; b < 2; ++b) {
@@ -358,6 +369,9 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
       CK(cudaEventCreateWithFlags(&c->join[j], cudaEventDisableTiming));
     }
     CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&c->tstream, cudaStreamNonBlocking));
+    for (int j = 0; j < 3; ++j) CK(cudaEventCreateWithFlags(&c->kdone[j], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->tjoin, cudaEventDisableTiming));
     CK(cudaStreamSynchronize(c->stream));
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
@@ -370,6 +384,12 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
       c->minb[sp] = std::min(4, mb);
       int bps = transport_max_blocks_per_sm(o.precision, sp, c->minb[sp], o.block_size);
       c->grid[sp] = sms * (bps < 1 ? 1 : bps);
+    }
+    if (o.fused) {
+      int mb = o.blocks_per_sm > 0 ? o.blocks_per_sm : (o.precision ? 2 : 1);
+      c->fminb = std::min(4, mb);
+      const int bps = fused_max_blocks_per_sm(o.precision, c->fminb, o.block_size);
+      c->fgrid = sms * (bps < 1 ? 1 : bps);
     }
   }
   c->slots.init(ms);
@@ -562,25 +582,48 @@ static bool timing(const adept_ctx* c) { return (c->opt.flags & (ADEPT_FLAG_TIME
 static bool timing_species(const adept_ctx* c) { return (c->opt.flags & ADEPT_FLAG_TIME_SPECIES) != 0; }
 
 // the generations of one chunk; timing events of status buffer b are ev[4 G b ...]
+// Timing events are recorded on tstream: the start one after the generation's fork, an end
+// one after each kernel it times. tstream joins the chain only at the end of the chunk, so
+// the records never delay the next generation.
 static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b) {
   cudaError_t e = cudaMemsetAsync(&c->P.ctrl->done_count[b], 0, sizeof(uint32_t), c->stream);
-  // fork e- (main stream), e+ and gamma (side streams), join, close: per generation
   const unsigned rf = cudaEventRecordExternal;
+  const bool T = timing(c), TS = timing_species(c);
   cudaEvent_t* ev = c->ev.empty() ? nullptr : c->ev.data() + 4 * gens * b;
+  cudaStream_t ts = c->tstream;
+  // record end event slot `at` on tstream once `done` (recorded on stream s) has happened
+  auto time_end = [&](cudaStream_t s, cudaEvent_t done, int at) {
+    if (e == cudaSuccess) e = cudaEventRecord(done, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ts, done, 0);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[at], ts, rf);
+  };
   for (int k = 0; k < gens && e == cudaSuccess; ++k) {
     e = cudaEventRecord(c->fork, c->stream);
-    if (e == cudaSuccess && timing(c)) e = cudaEventRecordWithFlags(ev[4 * k], c->stream, rf);
+    if (T) {
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ts, c->fork, 0);
+      if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[4 * k], ts, rf);
+    }
+    if (c->opt.fused) {  // one kernel per generation; its last block closes it
+      if (e == cudaSuccess) e = launch_fused_generation(c->P, c->opt.precision, c->fminb, c->fgrid, c->block, c->stream);
+      if (T) time_end(c->stream, c->kdone[0], 4 * k + 1);
+      continue;
+    }
+    // fork e- (main stream), e+ and gamma (side streams), join, close
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->side[j], c->fork, 0);
     cudaStream_t st[3] = {c->side[1], c->stream, c->side[0]};  // gamma, e-, e+
     for (int sp : {0, 1, 2}) {
       if (e == cudaSuccess) e = launch_transport(c->P, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, st[sp]);
-      if (e == cudaSuccess && timing_species(c)) e = cudaEventRecordWithFlags(ev[4 * k + 1 + sp], st[sp], rf);
+      if (TS) time_end(st[sp], c->kdone[sp], 4 * k + 1 + sp);
     }
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventRecord(c->join[j], c->side[j]);
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->stream, c->join[j], 0);
-    // without the per-species split: one end event after the join
-    if (e == cudaSuccess && timing(c) && !timing_species(c)) e = cudaEventRecordWithFlags(ev[4 * k + 1], c->stream, rf);
+    // without the per-species split: one end event once all three kernels have ended
+    if (T && !TS) time_end(c->stream, c->kdone[0], 4 * k + 1);
     if (e == cudaSuccess) e = launch_close_generation(c->P, c->stream);
+  }
+  if (T && e == cudaSuccess) {
+    e = cudaEventRecord(c->tjoin, ts);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->tjoin, 0);
   }
   if (e == cudaSuccess) e = launch_finish(c->P, b, c->stream);
   return e;
@@ -617,7 +660,7 @@ static int launch_chunk(adept_ctx* c, int b) {
   } else {
     CK(enqueue_generations(c, 1, b));
   }
-  c->stats.launches += 4 * gens + 2;
+  c->stats.launches += (c->opt.fused ? 1 : 4) * gens + 2;
   CK(cudaMemcpyAsync(c->h_ctrl[b], c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_done[b], c->P.evt.done_list[b], sizeof(uint32_t) * kDoneChunk, cudaMemcpyDeviceToHost,
                      c->stream));
@@ -996,6 +1039,10 @@ extern "C" void adept_destroy(adept_ctx* c) {
     if (c->join[j]) cudaEventDestroy(c->join[j]);
   }
   if (c->fork) cudaEventDestroy(c->fork);
+  if (c->tstream) { cudaStreamSynchronize(c->tstream); cudaStreamDestroy(c->tstream); }
+  for (int j = 0; j < 3; ++j)
+    if (c->kdone[j]) cudaEventDestroy(c->kdone[j]);
+  if (c->tjoin) cudaEventDestroy(c->tjoin);
   for (int b = 0; b < 2; ++b) {
     if (c->h_ctrl[b]) cudaFreeHost(c->h_ctrl[b]);
     if (c->h_done[b]) cudaFreeHost(c->h_done[b]);

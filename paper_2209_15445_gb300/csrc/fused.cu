@@ -1,0 +1,89 @@
+// One kernel per generation for all three species (S11, paper Sec. 3 and Sec. 5).
+//
+// Every warp takes the 32-track tiles of the concatenated gamma, e- and e+ queues in a
+// warp-strided order, species by species, in three consecutive loops (so that the register
+// allocation of one species' step does not overlap another's). The last block to finish
+// closes the generation (publishes the next queue sizes and advances gen); nothing waits
+// for anything, so the kernel needs no co-residency. Chained in a CUDA graph this is one
+// kernel node per generation instead of a fork, three species kernels, a join and a close
+// kernel, and the species share the SMs until the generation's last tile.
+#include <cuda_runtime.h>
+
+#include "layout.h"
+#include "transport.cuh"
+
+namespace adept {
+
+// index of this warp's first tile of the next segment of length `len`, given its first
+// tile `first` in the current segment (warp-strided order over the concatenation)
+__device__ __forceinline__ uint32_t next_first(uint32_t first, uint32_t len, uint32_t stride) {
+  if (first >= len) return first - len;
+  const uint32_t k = (len - first + stride - 1) / stride;  // tiles this warp took in the segment
+  return first + k * stride - len;
+}
+
+template <class R, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_fused_generation(Params P) {
+  __shared__ WarpRing<R> rings[8];
+  __shared__ unsigned long long s_cnt[6];
+  WarpRing<R>& ring = rings[threadIdx.x >> 5];
+  if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t wpb = blockDim.x >> 5;
+  const uint32_t nwarps = gridDim.x * wpb;
+  const int p = __ldcg(&P.ctrl->gen) & 1;
+  const uint32_t n0 = min(__ldcg(&P.ctrl->count[p][0]), P.cap);
+  const uint32_t n1 = min(__ldcg(&P.ctrl->count[p][1]), P.cap);
+  const uint32_t n2 = min(__ldcg(&P.ctrl->count[p][2]), P.cap);
+  const uint32_t T0 = (n0 + 31) >> 5, T1 = (n1 + 31) >> 5, T2 = (n2 + 31) >> 5;
+  unsigned long long nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
+  uint32_t head = 0, tail = 0;
+  uint32_t first = blockIdx.x * wpb + (threadIdx.x >> 5);
+  for (uint32_t t = first; t < T0; t += nwarps) run_tile<R, 0>(P, p, t << 5, n0, ring, head, tail, nsteps, ncreated);
+  if (tail != head) { drain<R, 0>(P, p, ring, head, tail - head, ncreated); head = tail; }
+  __syncwarp();
+  first = next_first(first, T0, nwarps);
+  for (uint32_t t = first; t < T1; t += nwarps) run_tile<R, 1>(P, p, t << 5, n1, ring, head, tail, nsteps, ncreated);
+  if (tail != head) { drain<R, 1>(P, p, ring, head, tail - head, ncreated); head = tail; }
+  __syncwarp();
+  first = next_first(first, T1, nwarps);
+  for (uint32_t t = first; t < T2; t += nwarps) run_tile<R, 2>(P, p, t << 5, n2, ring, head, tail, nsteps, ncreated);
+  if (tail != head) drain<R, 2>(P, p, ring, head, tail - head, ncreated);
+  if ((threadIdx.x & 31) == 0)
+    for (int k = 0; k < 3; ++k) {
+      if (nsteps[k]) atomicAdd(&s_cnt[k], nsteps[k]);
+      if (ncreated[k]) atomicAdd(&s_cnt[3 + k], ncreated[k]);
+    }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int k = 0; k < 3; ++k) {
+    if (s_cnt[k]) atomicAdd(&P.ctrl->steps[k], s_cnt[k]);
+    if (s_cnt[3 + k]) atomicAdd(&P.ctrl->created[k], s_cnt[3 + k]);
+  }
+  // last block out closes the generation (its appends and every other block's are
+  // ordered before the ticket by the fence)
+  __threadfence();
+  if (atomicAdd(&P.ctrl->blocks_done, 1u) == gridDim.x - 1) {
+    P.ctrl->blocks_done = 0;
+    close_generation(P);
+  }
+}
+
+// Variants: FP32 physics for 2 or 3 resident 256-thread blocks per SM, FP64 for 1 or 2.
+static const void* fused_fn(int precision, int minb) {
+  if (precision) return minb >= 3 ? (const void*)k_fused_generation<float, 3> : (const void*)k_fused_generation<float, 2>;
+  return minb >= 2 ? (const void*)k_fused_generation<double, 2> : (const void*)k_fused_generation<double, 1>;
+}
+
+int fused_max_blocks_per_sm(int precision, int minb, int block) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_fn(precision, minb), block, 0) != cudaSuccess) return 0;
+  return n;
+}
+
+cudaError_t launch_fused_generation(const Params& P, int precision, int minb, int grid, int block, cudaStream_t st) {
+  void* args[] = {const_cast<Params*>(&P)};
+  return cudaLaunchKernel(fused_fn(precision, minb), dim3(grid), dim3(block), args, 0, st);
+}
+
+}  // namespace adept

@@ -71,7 +71,7 @@ struct TrackSoA {
 struct Ctrl {
   uint32_t gen;               // generations run; parity gen & 1 holds the current queues
   uint32_t count[2][3];       // queue sizes [parity][species]
-  uint32_t blocks_done;       // last-block detection in the step kernel
+  uint32_t blocks_done;       // finished blocks of the fused generation kernel (last one closes)
   uint32_t done_count[2];     // events found finished by the finish pass of a chunk (per buffer)
   uint32_t log_n;             // rows written to the generation log
   uint32_t error;             // first device-detected error code (0 = none)
@@ -97,7 +97,8 @@ struct Params {
   GeoView geo;
   const MatDev* mat;
   TableView tab;
-  TrackSoA q[2][3];     // [parity][species]
+  TrackSoA q[2][3];     // [parity][species] (host copy; kernels index qd)
+  const TrackSoA* qd;   // the same six descriptors in device memory, [3 * parity + species]
   uint32_t cap;         // tracks per species per buffer
   Ctrl* ctrl;
   EventView evt;
@@ -151,5 +152,8 @@ cudaError_t launch_probe_distance(const Params& P, int prec, const double* pos, 
 cudaError_t launch_probe_sample(const Params& P, int which, int m, int prec, double E, uint32_t event,
                                 int n, double* out, cudaStream_t st);
 int transport_max_blocks_per_sm(int precision, int species, int minb, int block);
+// one kernel per generation for all species; its last block closes the generation
+cudaError_t launch_fused_generation(const Params& P, int precision, int minb, int grid, int block, cudaStream_t st);
+int fused_max_blocks_per_sm(int precision, int minb, int block);
 
 }  // namespace adept

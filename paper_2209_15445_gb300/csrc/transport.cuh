@@ -1,0 +1,417 @@
+// Device side of one transport step, shared by the per-species generation kernels
+// (kernels.cu) and the persistent multi-generation kernel (persistent.cu): track load and
+// store, phase A (S1-S8), phase B (S9), scoring (S10), warp-aggregated appends and the
+// per-warp ring of deferred interactions.
+//
+// Queue descriptors are read from P.qd (device memory) with a runtime parity index:
+// indexing the kernel-parameter copy P.q that way makes the compiler copy the parameter
+// block to local memory once several species paths share a kernel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "layout.h"
+
+namespace adept {
+
+template <class R> struct Trk {
+  double x, y, z;
+  R u[3];
+  double E;
+  unsigned long long id;
+  uint32_t ev, step, nav;
+};
+
+// Queue loads are streaming (ld.global.cs): each slot is read once per generation.
+template <class R>
+__device__ __forceinline__ void load_track(const TrackSoA& q, uint32_t i, Trk<R>& t);
+template <>
+__device__ __forceinline__ void load_track<double>(const TrackSoA& q, uint32_t i, Trk<double>& t) {
+  t.x = __ldcs(q.x + i); t.y = __ldcs(q.y + i); t.z = __ldcs(q.z + i);
+  t.u[0] = __ldcs(q.ux + i); t.u[1] = __ldcs(q.uy + i); t.u[2] = __ldcs(q.uz + i);
+  t.E = __ldcs(q.E + i);
+  t.id = __ldcs(q.id + i);
+  t.ev = __ldcs(q.ev + i);
+  t.step = __ldcs(q.step + i);
+  t.nav = __ldcs(q.nav + i);
+}
+template <>
+__device__ __forceinline__ void load_track<float>(const TrackSoA& q, uint32_t i, Trk<float>& t) {
+  const double2 a = __ldcs(q.xy + i), b = __ldcs(q.zE + i);
+  const float4 c = __ldcs(q.un + i);
+  const uint4 d = __ldcs(q.meta + i);
+  t.x = a.x; t.y = a.y; t.z = b.x; t.E = b.y;
+  t.u[0] = c.x; t.u[1] = c.y; t.u[2] = c.z;
+  t.nav = __float_as_uint(c.w);
+  t.id = (unsigned long long)d.x | ((unsigned long long)d.y << 32);
+  t.ev = d.z;
+  t.step = d.w;
+}
+
+template <class R>
+__device__ __forceinline__ void store_track(const TrackSoA& q, uint32_t i, double x, double y, double z, R ux,
+                                            R uy, R uz, double E, unsigned long long id, uint32_t ev,
+                                            uint32_t step, uint32_t nav);
+template <>
+__device__ __forceinline__ void store_track<double>(const TrackSoA& q, uint32_t i, double x, double y, double z,
+                                                    double ux, double uy, double uz, double E, unsigned long long id,
+                                                    uint32_t ev, uint32_t step, uint32_t nav) {
+  q.x[i] = x; q.y[i] = y; q.z[i] = z;
+  q.ux[i] = ux; q.uy[i] = uy; q.uz[i] = uz;
+  q.E[i] = E;
+  q.id[i] = id;
+  q.ev[i] = ev;
+  q.step[i] = step;
+  q.nav[i] = nav;
+}
+template <>
+__device__ __forceinline__ void store_track<float>(const TrackSoA& q, uint32_t i, double x, double y, double z,
+                                                   float ux, float uy, float uz, double E, unsigned long long id,
+                                                   uint32_t ev, uint32_t step, uint32_t nav) {
+  q.xy[i] = make_double2(x, y);
+  q.zE[i] = make_double2(z, E);
+  q.un[i] = make_float4(ux, uy, uz, __uint_as_float(nav));
+  q.meta[i] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), ev, step);
+}
+
+template <class R> __device__ __forceinline__ const typename Pair2<R>::T* tab_g(const TableView& T);
+template <> __device__ __forceinline__ const double2* tab_g<double>(const TableView& T) { return T.g64; }
+template <> __device__ __forceinline__ const float2* tab_g<float>(const TableView& T) { return T.g32; }
+template <class R> __device__ __forceinline__ const typename Pair2<R>::T* tab_e(const TableView& T);
+template <> __device__ __forceinline__ const double2* tab_e<double>(const TableView& T) { return T.e64; }
+template <> __device__ __forceinline__ const float2* tab_e<float>(const TableView& T) { return T.e32; }
+template <class R> __device__ __forceinline__ const typename Pair2<R>::T* tab_p(const TableView& T);
+template <> __device__ __forceinline__ const double2* tab_p<double>(const TableView& T) { return T.p64; }
+template <> __device__ __forceinline__ const float2* tab_p<float>(const TableView& T) { return T.p32; }
+template <class R> __device__ __forceinline__ const R* range_nodes(const TableView& T, bool pos);
+template <> __device__ __forceinline__ const double* range_nodes<double>(const TableView& T, bool pos) { return pos ? T.rp64 : T.re64; }
+template <> __device__ __forceinline__ const float* range_nodes<float>(const TableView& T, bool pos) { return pos ? T.rp32 : T.re32; }
+
+__device__ __forceinline__ bool on(uint32_t mask, uint32_t bit) { return mask == 0u || (mask & bit); }
+
+enum Outcome { kDead = 0, kAlive = 1, kInteract = 2 };
+
+// Phase A of one step of one track of species S (0 gamma, 1 e-, 2 e+) -- paper Sec. 3:
+// every live track advances by one step per generation. Cross sections and range at the
+// pre-step energy (S2), sampled interaction length (S3), step limit (S4), boundary
+// distance (S5/S6), move, continuous loss (S7) and boundary crossing (S8). A step that
+// ends in a discrete interaction returns kInteract with the chosen process; the
+// interaction itself (S9) runs later on a full warp. dep is the energy to score in
+// dep_bin; sec receives the two photons of a positron that stops.
+template <class R, int S>
+__device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>& sec, double& dep, int& dep_bin,
+                                              uint32_t& pstep, int& proc) {
+  constexpr int q = S == 1 ? -1 : (S == 2 ? 1 : 0);
+  const double rest = S == 2 ? 2.0 * kMe : 0.0;
+  const int vol = (int)(t.nav & 0xFFFFu);
+  uint32_t vac = t.nav >> 16;
+  const int m = __ldg(P.geo.vol_mat + vol);
+  dep_bin = __ldg(P.geo.vol_bin + vol);
+  sec.n = 0;
+  dep = 0.0;
+  const uint32_t step = t.step;
+  pstep = step;
+  if (step >= P.max_steps) { atomicAdd(P.evt.killed + t.ev, t.E + rest); return kDead; }
+  if (m < 0) {
+    if (vac >= P.max_vac) { atomicAdd(P.evt.killed + t.ev, t.E + rest); return kDead; }
+    ++vac;
+  } else {
+    vac = 0;
+  }
+  const R tcut = (R)P.tcut;
+  const R Er = to_r<R>(t.E);
+  Stream<R> rs(P.seed, __ldg(P.evt.key + t.ev), t.id, step);
+  if (Er < tcut) {
+    dep = t.E;
+    if (S == 2) annihilate_at_rest<R>(rs, sec);
+    return kDead;
+  }
+  R u0, u1;
+  rs.block0(&u0, &u1);
+
+  // S2: cross sections and range at the pre-step energy
+  R sg0 = 0, sg1 = 0, sg2 = 0, Rr = 0;
+  int bin = 0;
+  if (m >= 0) {
+    R tt;
+    grid_pos<R>(t.E, &bin, &tt);
+    if (S == 0) {
+      const auto* rec = tab_g<R>(P.tab) + ((size_t)m * kNNode + bin) * kNTabG;
+      if (on(P.process_mask, 1u << 0)) sg0 = lerp_rec<R>(rec, 0, tt);
+      if (on(P.process_mask, 1u << 1)) sg1 = lerp_rec<R>(rec, 1, tt);
+      if (on(P.process_mask, 1u << 2)) sg2 = lerp_rec<R>(rec, 2, tt);
+    } else if (S == 1) {
+      const auto* rec = tab_e<R>(P.tab) + ((size_t)m * kNNode + bin) * kNTabE;
+      Rr = lerp_rec<R>(rec, 1, tt);
+      if (on(P.process_mask, 1u << 3)) sg0 = lerp_rec<R>(rec, 2, tt);
+      if (on(P.process_mask, 1u << 4)) sg1 = lerp_rec<R>(rec, 3, tt);
+    } else {
+      const auto* rec = tab_p<R>(P.tab) + ((size_t)m * kNNode + bin) * kNTabP;
+      Rr = lerp_rec<R>(rec, 1, tt);
+      if (on(P.process_mask, 1u << 5)) sg0 = lerp_rec<R>(rec, 2, tt);
+      if (on(P.process_mask, 1u << 6)) sg1 = lerp_rec<R>(rec, 3, tt);
+      if (on(P.process_mask, 1u << 7)) sg2 = lerp_rec<R>(rec, 4, tt);
+    }
+  }
+  sg0 = sg0 < (R)0 ? (R)0 : sg0;
+  sg1 = sg1 < (R)0 ? (R)0 : sg1;
+  sg2 = sg2 < (R)0 ? (R)0 : sg2;
+  const R stot = sg0 + sg1 + sg2;
+  // S3/S4: sampled interaction length and the range-based step limit
+  R s_phys = stot > (R)0 ? M<R>::fdiv(-M<R>::flog(u0), stot) : M<R>::big();
+  if (q != 0 && m >= 0) {
+    const R smax = (Rr <= (R)kRhoF) ? Rr : ((R)kAlphaR * Rr > (R)kRhoF ? (R)kAlphaR * Rr : (R)kRhoF);
+    if (smax < s_phys) s_phys = smax;
+  }
+  // S5/S6: distance to the boundary along the straight line or helix
+  int next;
+  const bool field = (q != 0) && (P.field_T != 0.0);
+  const R s_geom = field ? helix_distance<R>(P.geo, P.field_T, t.E, q, t.x, t.y, t.z, t.u, vol, &next)
+                         : straight_distance<R>(P.geo, t.x, t.y, t.z, t.u, vol, &next);
+  const bool boundary = s_geom <= s_phys;
+  const R s = boundary ? s_geom : s_phys;
+  if (field) {
+    helix_move<R>(P.field_T, t.E, q, s, &t.x, &t.y, &t.z, t.u);
+  } else {
+    t.x += to_d<R>(s * t.u[0]);
+    t.y += to_d<R>(s * t.u[1]);
+    t.z += to_d<R>(s * t.u[2]);
+  }
+  if (boundary && P.geo.kind == 0 && next >= 0) t.z = __ldg(P.geo.bnd + (t.u[2] > (R)0 ? vol + 1 : vol));
+  t.step = step + 1;
+  if (P.steplen && s > (R)0 && s < M<R>::big()) {
+    // validation histogram of step lengths: bin = floor(log2 s[mm]) + 40
+    int b = ilogb(s) + 40;
+    b = b < 0 ? 0 : (b > 63 ? 63 : b);
+    atomicAdd(P.steplen + 64 * S + b, 1ull);
+  }
+
+  // S7: continuous loss by inverting the range table
+  if (q != 0 && m >= 0) {
+    R Epr = 0;
+    if (s < Rr) Epr = inverse_range<R>(range_nodes<R>(P.tab, S == 2) + (size_t)m * kNNode, Rr - s, bin + 1);
+    const double Ep = (Epr > Er) ? t.E : to_d<R>(Epr);
+    dep += t.E - Ep;
+    t.E = Ep;
+    if (Epr < tcut) {
+      dep += t.E;
+      t.E = 0.0;
+      if (S == 2) annihilate_at_rest<R>(rs, sec);
+      return kDead;
+    }
+  }
+  // S8: boundary crossing
+  if (boundary) {
+    if (next < 0) { atomicAdd(P.evt.leaked + t.ev, t.E + rest); return kDead; }
+    t.nav = (uint32_t)next | (vac << 16);
+    return kAlive;
+  }
+  t.nav = (uint32_t)vol | (vac << 16);
+  // S9 (deferred): the process is chosen with u1 over the fixed order
+  const R xs = u1 * stot;
+  proc = (S == 1) ? 1 : 2;
+  if (xs < sg0) proc = 0;
+  else if (xs < sg0 + sg1) proc = 1;
+  return kInteract;
+}
+
+// Phase B: the discrete interaction (S9) of a track queued by phase A. Its random stream
+// is rebuilt from (event, id, step): block 0 was consumed in phase A, the models draw
+// from block 1 on. Returns whether the parent survives (with its new state in t).
+template <class R, int S>
+__device__ __forceinline__ bool step_interact(const Params& P, Trk<R>& t, uint32_t pstep, int proc, Ixn<R>& sec,
+                                              double& dep) {
+  const int m = __ldg(P.geo.vol_mat + (int)(t.nav & 0xFFFFu));
+  Stream<R> rs(P.seed, __ldg(P.evt.key + t.ev), t.id, pstep);
+  const double Tc = __ldg(P.tab.Tc + m), kc = __ldg(P.tab.kc + m);
+  const R tcut = (R)P.tcut;
+  sec.happened = false;
+  sec.n = 0;
+  dep = 0.0;
+  if (S == 0) {
+    if (proc == 0) compton<R>(rs, t.E, t.u, sec);
+    else if (proc == 1) pair<R>(rs, t.E, t.u, sec);
+    else photo<R>(t.E, t.u, sec);
+  } else if (S == 1) {
+    if (proc == 0) moller<R>(rs, t.E, Tc, t.u, sec);
+    else brem<R>(rs, t.E, kc, t.u, sec);
+  } else {
+    if (proc == 0) bhabha<R>(rs, t.E, Tc, t.u, sec);
+    else if (proc == 1) brem<R>(rs, t.E, kc, t.u, sec);
+    else annihilate<R>(rs, t.E, t.u, sec);
+  }
+  if (!sec.happened) { sec.n = 0; return true; }
+  // secondaries other than positrons below the tracking cut deposit locally
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    if (k < sec.n && sec.sp[k] != 2 && to_r<R>(sec.E[k]) < tcut) { dep += sec.E[k]; sec.sp[k] = -1; }
+  if (!sec.parent_alive) return false;
+  t.E = sec.parent_E;
+  t.u[0] = sec.pd[0]; t.u[1] = sec.pd[1]; t.u[2] = sec.pd[2];
+  if (S == 0 && to_r<R>(t.E) < tcut) { dep += t.E; return false; }
+  return true;
+}
+
+__device__ __forceinline__ void score(const Params& P, uint32_t ev, int bin, double dep) {
+  if (bin >= 0 && __double_as_longlong(dep) != 0) atomicAdd(P.evt.edep + (size_t)ev * P.geo.n_bins + bin, dep);
+}
+
+// Warp-aggregated appends (S9/S11): every lane of the warp calls this; a lane passes the
+// surviving track (alive) and up to two secondaries, and gets consecutive slots of the
+// next queues through one atomic per species per warp.
+template <class R, int S>
+__device__ __forceinline__ void emit(const Params& P, int p, const Trk<R>& t, bool alive, const Ixn<R>& sec,
+                                     uint32_t pstep, unsigned long long* ncreated) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  const bool f1 = sec.n > 0 && sec.sp[0] >= 0;
+  const bool f2 = sec.n > 1 && sec.sp[1] >= 0;
+  const int s1 = f1 ? sec.sp[0] : -1, s2 = f2 ? sec.sp[1] : -1;
+  uint32_t b0[3], b1[3], b2[3], wbase[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    b0[k] = __ballot_sync(0xFFFFFFFFu, alive && k == S);
+    b1[k] = __ballot_sync(0xFFFFFFFFu, s1 == k);
+    b2[k] = __ballot_sync(0xFFFFFFFFu, s2 == k);
+    const uint32_t cnt = __popc(b0[k]) + __popc(b1[k]) + __popc(b2[k]);
+    uint32_t bk = 0;
+    if (lane == 0 && cnt) bk = atomicAdd(&P.ctrl->count[p ^ 1][k], cnt);
+    wbase[k] = __shfl_sync(0xFFFFFFFFu, bk, 0);
+    ncreated[k] += __popc(b1[k]) + __popc(b2[k]);
+  }
+  const TrackSoA* nq = P.qd + 3 * (p ^ 1);
+  // pick entry k of a 3-array without dynamic indexing (which would place it in local memory)
+  auto pick = [](const uint32_t* a, int k) { return k == 0 ? a[0] : (k == 1 ? a[1] : a[2]); };
+  if (alive) {
+    const uint32_t d = wbase[S] + __popc(b0[S] & lt);
+    if (d < P.cap) {
+      store_track<R>(nq[S], d, t.x, t.y, t.z, t.u[0], t.u[1], t.u[2], t.E, t.id, t.ev, t.step, t.nav);
+    } else {
+      atomicAdd(&P.ctrl->overflow, 1ull);
+      atomicAdd(P.evt.killed + t.ev, t.E + (S == 2 ? 2.0 * kMe : 0.0));
+    }
+  }
+  const uint32_t vnav = t.nav & 0xFFFFu;  // secondaries start with no vacuum history
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int sk = k == 0 ? s1 : s2;
+    if (sk < 0) continue;
+    const uint32_t before = __popc(pick(b0, sk)) + (k == 1 ? __popc(pick(b1, sk)) : 0u);
+    const uint32_t mine = __popc((k == 0 ? pick(b1, sk) : pick(b2, sk)) & lt);
+    const uint32_t d = pick(wbase, sk) + before + mine;
+    if (d < P.cap) {
+      const unsigned long long cid = child_id(P.seed, __ldg(P.evt.key + t.ev), t.id, pstep, (uint32_t)k);
+      store_track<R>(nq[sk], d, t.x, t.y, t.z, sec.d[k][0], sec.d[k][1], sec.d[k][2], sec.E[k], cid, t.ev, 0u,
+                     vnav);
+    } else {
+      atomicAdd(&P.ctrl->overflow, 1ull);
+      atomicAdd(P.evt.killed + t.ev, sec.E[k] + (sk == 2 ? 2.0 * kMe : 0.0));
+    }
+  }
+}
+
+// Per-warp ring of tracks waiting for their discrete interaction (64 entries: phase A of
+// one tile adds at most 32 to fewer than 32 waiting, so nothing is overwritten before it
+// is processed). Interactions then run 32 at a time on a full warp instead of on the few
+// lanes of each tile that happened to interact.
+constexpr int kRing = 64;
+template <class R> struct WarpRing {
+  double x[kRing], y[kRing], z[kRing], E[kRing];
+  unsigned long long id[kRing];
+  R ux[kRing], uy[kRing], uz[kRing];
+  uint32_t ev[kRing], pstep[kRing], nav[kRing], proc[kRing];
+};
+
+template <class R, int S>
+__device__ __forceinline__ void drain(const Params& P, int p, WarpRing<R>& ring, uint32_t head, uint32_t count,
+                                      unsigned long long* ncreated) {
+  const int lane = threadIdx.x & 31;
+  const bool have = (uint32_t)lane < count;
+  Trk<R> t;
+  t.nav = 0; t.ev = 0; t.id = 0; t.E = 0.0; t.step = 0;
+  uint32_t pstep = 0;
+  Ixn<R> sec;
+  sec.n = 0;
+  bool alive = false;
+  if (have) {
+    const uint32_t j = (head + lane) & (kRing - 1);
+    t.x = ring.x[j]; t.y = ring.y[j]; t.z = ring.z[j]; t.E = ring.E[j];
+    t.u[0] = ring.ux[j]; t.u[1] = ring.uy[j]; t.u[2] = ring.uz[j];
+    t.id = ring.id[j]; t.ev = ring.ev[j]; t.nav = ring.nav[j];
+    pstep = ring.pstep[j];
+    t.step = pstep + 1;
+    double dep = 0.0;
+    alive = step_interact<R, S>(P, t, pstep, (int)ring.proc[j], sec, dep);
+    score(P, t.ev, __ldg(P.geo.vol_bin + (int)(t.nav & 0xFFFFu)), dep);
+  }
+  __syncwarp();
+  emit<R, S>(P, p, t, alive, sec, pstep, ncreated);
+}
+
+// One warp takes 32 consecutive tracks of species S: phase A for each, appends the
+// survivors, queues the interactions and runs full warps of them as they accumulate.
+template <class R, int S>
+__device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, uint32_t n, WarpRing<R>& ring,
+                                         uint32_t& head, uint32_t& tail, unsigned long long* nsteps,
+                                         unsigned long long* ncreated) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t i = base + lane;
+  const bool active = i < n;
+  Trk<R> t;
+  t.nav = 0; t.ev = 0; t.id = 0; t.E = 0.0;
+  Ixn<R> sec;
+  sec.n = 0;
+  uint32_t pstep = 0;
+  int outcome = kDead, proc = 0;
+  if (active) {
+    load_track<R>(P.qd[3 * p + S], i, t);
+    double dep = 0.0;
+    int dep_bin = -1;
+    outcome = step_transport<R, S>(P, t, sec, dep, dep_bin, pstep, proc);
+    // S10: score the step's deposit in (event, layer, material)
+    score(P, t.ev, dep_bin, dep);
+  }
+  nsteps[S] += __popc(__ballot_sync(0xFFFFFFFFu, active));
+  emit<R, S>(P, p, t, outcome == kAlive, sec, pstep, ncreated);
+  const uint32_t need = __ballot_sync(0xFFFFFFFFu, outcome == kInteract);
+  if (outcome == kInteract) {
+    const uint32_t j = (tail + __popc(need & ((1u << lane) - 1u))) & (kRing - 1);
+    ring.x[j] = t.x; ring.y[j] = t.y; ring.z[j] = t.z; ring.E[j] = t.E;
+    ring.ux[j] = t.u[0]; ring.uy[j] = t.u[1]; ring.uz[j] = t.u[2];
+    ring.id[j] = t.id; ring.ev[j] = t.ev; ring.nav[j] = t.nav; ring.pstep[j] = pstep; ring.proc[j] = (uint32_t)proc;
+  }
+  tail += __popc(need);
+  __syncwarp();
+  while (tail - head >= 32u) {
+    drain<R, S>(P, p, ring, head, 32u, ncreated);
+    head += 32u;
+    __syncwarp();
+  }
+}
+
+// Close a generation once the species kernels are done: publish the next queue sizes
+// (clamped to the capacity; overflow was counted), log them, empty the consumed queues
+// and advance gen, whose parity selects the buffers. One thread runs it.
+__device__ __forceinline__ void close_generation(const Params& P) {
+  volatile Ctrl* c = P.ctrl;
+  const uint32_t gen = c->gen;
+  const int p = gen & 1;
+  uint32_t nn[3];
+  for (int k = 0; k < 3; ++k) {
+    uint32_t m = c->count[p ^ 1][k];
+    if (m > P.cap) m = P.cap;
+    nn[k] = m;
+    c->count[p ^ 1][k] = m;
+    c->count[p][k] = 0;
+  }
+  const uint32_t ln = c->log_n;
+  if (ln < P.max_log) {
+    for (int k = 0; k < 3; ++k) P.gen_log[3 * ln + k] = nn[k];
+    c->log_n = ln + 1;
+  }
+  c->generations = c->generations + 1;
+  __threadfence();
+  c->gen = gen + 1;
+}
+
+}  // namespace adept
