@@ -22,6 +22,8 @@ _lib = None
 
 NNODE = 289
 P_COMPT, P_CONV, P_PHOTO, P_EIONI, P_EBREM, P_PIONI, P_PBREM, P_ANNIH = (1 << i for i in range(8))
+# optional continuous physics of or_run_opts.physics
+PHYS_MSC, PHYS_FLUCT = 1, 2
 
 # sampler ids of or_sample
 S_COMPTON, S_PAIR, S_MOLLER, S_BHABHA, S_BREM, S_ANNIH, S_ANNIH_REST = range(7)
@@ -45,7 +47,8 @@ def build(force: bool = False) -> str:
 
 class _RunOpts(C.Structure):
     _fields_ = [("seed", C.c_uint32), ("process_mask", C.c_uint32), ("max_steps", C.c_uint32),
-                ("max_vacuum_steps", C.c_uint32), ("n_threads", C.c_int), ("max_gen", C.c_int)]
+                ("max_vacuum_steps", C.c_uint32), ("n_threads", C.c_int), ("max_gen", C.c_int),
+                ("physics", C.c_uint32), ("msc_range_factor", C.c_double)]
 
 
 class _Result(C.Structure):
@@ -86,6 +89,9 @@ def lib():
             L.or_inverse_range.argtypes = [p, i, i, d]; L.or_inverse_range.restype = d
             L.or_node_energy.argtypes = [i]; L.or_node_energy.restype = d
             L.or_sample.argtypes = [p, i, i, d, u32, u32, i, dp]
+            L.or_sample_continuous.argtypes = [p, i, i, i, d, d, u32, u32, i, dp]
+            L.or_msc_theta0.argtypes = [p, i, d, d]; L.or_msc_theta0.restype = d
+            L.or_fluct_sigma2.argtypes = [p, i, d, d, i]; L.or_fluct_sigma2.restype = d
             L.or_n_volumes.argtypes = [p]; L.or_n_volumes.restype = i
             L.or_n_bins.argtypes = [p]; L.or_n_bins.restype = i
             L.or_locate.argtypes = [p, dp, dp]; L.or_locate.restype = i
@@ -194,6 +200,15 @@ class Oracle:
         lib().or_sample(self.h, which, m, E, seed, event, n, _dp(out))
         return out
 
+    def msc_theta0(self, m, T, s): return lib().or_msc_theta0(self.h, m, T, s)
+    def fluct_sigma2(self, m, T, s, positron=False): return lib().or_fluct_sigma2(self.h, m, T, s, int(positron))
+
+    def sample_continuous(self, which, species, m, T, s, n, seed=1, event=0) -> np.ndarray:
+        """which 0: (n, 3) deflected directions of (0,0,1); which 1: (n, 2) loss and mean loss"""
+        out = np.zeros((n, 3 if which == 0 else 2))
+        lib().or_sample_continuous(self.h, which, species, m, T, s, seed, event, n, _dp(out))
+        return out
+
     def locate(self, pos, d):
         pos = np.ascontiguousarray(pos, np.float64); d = np.ascontiguousarray(d, np.float64)
         return lib().or_locate(self.h, _dp(pos), _dp(d))
@@ -211,7 +226,8 @@ class Oracle:
         return s, nx.value
 
     def transport(self, prim, seed=1, process_mask=0, max_steps=100000, max_vacuum_steps=1000,
-                  n_threads=None, max_gen=0, steplen=False, event_slot=None, n_events=None):
+                  n_threads=None, max_gen=0, steplen=False, event_slot=None, n_events=None,
+                  physics=0, msc_range_factor=0.0):
         """Transport primaries; tracks with the same event number form one event (slot
         order = first appearance) unless event_slot is given."""
         n = len(prim)
@@ -233,7 +249,7 @@ class Oracle:
         res.gen_hist = gen.ctypes.data_as(C.POINTER(C.c_uint64)) if max_gen > 0 else None
         res.steplen_hist = sl.ctypes.data_as(C.POINTER(C.c_uint64)) if steplen else None
         o = _RunOpts(seed, process_mask, max_steps, max_vacuum_steps,
-                     n_threads or os.cpu_count() or 1, max_gen)
+                     n_threads or os.cpu_count() or 1, max_gen, physics, msc_range_factor)
         pdg = np.ascontiguousarray(prim.pdg, np.int32)
         E = np.ascontiguousarray(prim.E, np.float64)
         pos = np.ascontiguousarray(prim.pos, np.float64)

@@ -735,6 +735,68 @@ typedef struct {
 
 static const int kMaxRejections = 1000;
 
+/* ------------------------------------------------------------------ continuous physics */
+/* the uniform pair of counter block blk of a (track, step) stream */
+static void stream_block(const stream_t* s, uint32_t blk, double* ua, double* ub) {
+  const uint32_t c[4] = {s->ctr[0], s->ctr[1], s->ctr[2], blk};
+  uint32_t w[4];
+  or_philox(c, s->key, w);
+  *ua = or_u01_f64(w[0], w[1]);
+  *ub = or_u01_f64(w[2], w[3]);
+}
+
+/* Highland's width of the projected scattering angle (PDG Review of Particle Physics,
+ * "Passage of particles through matter", multiple scattering through small angles):
+ * theta0 = 13.6 MeV / (beta c p) * z * sqrt(x/X0) * (1 + 0.038 ln(x z^2 / (X0 beta^2))),
+ * z = 1, at the pre-step energy. The bracket, negative only below x/X0 ~ 1e-11, is
+ * clamped at 0. */
+double or_msc_theta0(const or_ctx* c, int m, double T, double s) {
+  const double E = T + kMe, pc2 = T * (T + 2.0 * kMe);
+  const double beta2 = pc2 / (E * E), bcp = pc2 / E;
+  const double x = s * c->mat[m].invX0;
+  if (!(x > 0.0)) return 0.0;
+  double br = 1.0 + 0.038 * log(x / beta2);
+  if (br < 0.0) br = 0.0;
+  return 13.6 / bcp * sqrt(x) * br;
+}
+
+/* Bohr's variance of the energy lost over s to transfers up to Tu (the part of the loss
+ * that is continuous: Tu = min(production cut, largest transfer), T/2 for e-, T for e+):
+ * sigma^2 = 2 pi r_e^2 m c^2 n_el s Tu (1 - beta^2/2) / beta^2. */
+double or_fluct_sigma2(const or_ctx* c, int m, double T, double s, int positron) {
+  const mat_t* t = &c->mat[m];
+  const double E = T + kMe, beta2 = T * (T + 2.0 * kMe) / (E * E);
+  const double tmax = positron ? T : 0.5 * T;
+  const double tu = c->Tc[m] < tmax ? c->Tc[m] : tmax;
+  return 2.0 * kPi * kRe * kRe * kMe * t->n_el * s * tu * (1.0 - 0.5 * beta2) / beta2;
+}
+
+/* deflection by theta = theta0 sqrt(-2 ln ua) (the space angle of two independent Gaussian
+ * projected angles of width theta0), at most pi, azimuth 2 pi ub */
+static void msc_deflect(const stream_t* rs, double theta0, double u[3]) {
+  double ua, ub;
+  stream_block(rs, OR_MSC_BLOCK, &ua, &ub);
+  double th = theta0 * sqrt(-2.0 * log(ua));
+  if (th > kPi) th = kPi;
+  double out[3];
+  rotate_to(u, cos(th), 2.0 * kPi * ub, out);
+  normalize3(out);
+  memcpy(u, out, sizeof(out));
+}
+
+/* Gaussian loss about the mean, redrawn (at most 8 times, then the mean) until it lies in
+ * [0, 2 mean]; one Box-Muller normal per counter block */
+static double fluct_loss(const stream_t* rs, double mean, double sigma) {
+  for (uint32_t i = 0; i < 8; ++i) {
+    double ua, ub;
+    stream_block(rs, OR_FLUCT_BLOCK + i, &ua, &ub);
+    const double g = sqrt(-2.0 * log(ua)) * cos(2.0 * kPi * ub);
+    const double d = mean + sigma * g;
+    if (d >= 0.0 && d <= 2.0 * mean) return d;
+  }
+  return mean;
+}
+
 /* Compton, Klein-Nishina via Butcher & Messel composition-rejection (Nucl. Phys. 20 (1960)
  * 15; EGS4 SLAC-265 Sec. 2.9): eps = E'/E in [eps0, 1], eps0 = 1/(1+2 kappa), is drawn from
  * 1/eps (weight ln(1/eps0)) or from eps (weight (1-eps0^2)/2), then accepted with
@@ -951,6 +1013,27 @@ static void sample_annih_rest(stream_t* st, ixn_t* r) {
   r->T[0] = kMe; r->T[1] = kMe;
   r->dir[0][0] = st_ * cos(phi); r->dir[0][1] = st_ * sin(phi); r->dir[0][2] = ct;
   r->dir[1][0] = -r->dir[0][0]; r->dir[1][1] = -r->dir[0][1]; r->dir[1][2] = -r->dir[0][2];
+}
+
+void or_sample_continuous(const or_ctx* c, int which, int species, int m, double T, double s,
+                          uint32_t seed, uint32_t event, int n, double* out) {
+  for (int i = 0; i < n; ++i) {
+    stream_t st;
+    stream_init(&st, seed, event, (uint64_t)(i + 1), 0);
+    if (which == 0) {
+      double u[3] = {0.0, 0.0, 1.0};
+      msc_deflect(&st, or_msc_theta0(c, m, T, s), u);
+      memcpy(out + 3 * i, u, sizeof(u));
+    } else {
+      const double* Rt = species == 2 ? c->pos[m][1] : c->ele[m][1];
+      const double R = interp_nodes(Rt, T);
+      double Ep = s < R ? inverse_range_nodes(Rt, R - s) : 0.0;
+      if (Ep > T) Ep = T;
+      const double mean = T - Ep;
+      out[2 * i] = fluct_loss(&st, mean, sqrt(or_fluct_sigma2(c, m, T, s, species == 2)));
+      out[2 * i + 1] = mean;
+    }
+  }
 }
 
 void or_sample(const or_ctx* c, int which, int m, double E, uint32_t seed, uint32_t event, int n,
@@ -1201,8 +1284,14 @@ static int step_track(ev_t* e, trk_t* t, stack_t_* st) {
   const double stot = sig[0] + sig[1] + sig[2];
   const double s_int = stot > 0.0 ? -log(u0) / stot : kInf;
   double s_phys = s_int;
+  const int msc = (o->physics & OR_PHYS_MSC) != 0, fluct = (o->physics & OR_PHYS_FLUCT) != 0;
   if (q != 0 && m >= 0) {
-    const double smax = (R <= kRhoF) ? R : ((kAlphaR * R > kRhoF) ? kAlphaR * R : kRhoF);
+    double smax = (R <= kRhoF) ? R : ((kAlphaR * R > kRhoF) ? kAlphaR * R : kRhoF);
+    if (msc) {  /* multiple-scattering step limit */
+      const double f = o->msc_range_factor > 0.0 ? o->msc_range_factor : 0.04;
+      const double sm = (f * R > 0.01) ? f * R : 0.01;
+      if (sm < smax) smax = sm;
+    }
     if (smax < s_phys) s_phys = smax;
   }
 
@@ -1226,12 +1315,16 @@ static int step_track(ev_t* e, trk_t* t, stack_t_* st) {
   }
   t->step = step + 1;
 
-  /* continuous energy loss through the range table */
+  /* continuous energy loss through the range table; with fluctuations, a Gaussian loss
+   * about that mean for a track that survives the mean loss */
+  const double Tpre = t->T;
   if (q != 0 && m >= 0) {
     const double* Rt = (sp == 1) ? c->ele[m][1] : c->pos[m][1];
     double Epost = 0.0;
     if (s < R) Epost = inverse_range_nodes(Rt, R - s);
     if (Epost > t->T) Epost = t->T;
+    if (fluct && s < R && Epost >= c->tcut)
+      Epost = t->T - fluct_loss(&rs, t->T - Epost, sqrt(or_fluct_sigma2(c, m, t->T, s, sp == 2)));
     deposit(e, t->vol, t->T - Epost);
     t->T = Epost;
     if (t->T < c->tcut) {
@@ -1244,6 +1337,8 @@ static int step_track(ev_t* e, trk_t* t, stack_t_* st) {
       }
       return 0;
     }
+    /* multiple scattering: the direction at the end of the step */
+    if (msc && s > 0.0) msc_deflect(&rs, or_msc_theta0(c, m, Tpre, s), t->u);
   }
 
   if (boundary) {

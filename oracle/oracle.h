@@ -94,6 +94,25 @@ double or_node_energy(int i);
 void or_sample(const or_ctx* c, int which, int m, double E, uint32_t seed, uint32_t event, int n,
                double* out);
 
+/* ---- optional continuous physics (off unless or_run_opts.physics sets it) ----
+ * OR_PHYS_MSC: multiple Coulomb scattering of e+-, a Gaussian (Highland) deflection at the
+ *   end of every charged step, with the step limit s <= max(f R, 0.01 mm);
+ * OR_PHYS_FLUCT: Gaussian (Bohr) fluctuations of the restricted continuous loss. */
+#define OR_PHYS_MSC   (1u << 0)
+#define OR_PHYS_FLUCT (1u << 1)
+#define OR_MSC_BLOCK   0x40000000u /* Philox counter block of the deflection */
+#define OR_FLUCT_BLOCK 0x40000001u /* first block of the fluctuation draws */
+/* Highland's theta0 [rad] of an e+- of kinetic energy T over path s in material m */
+double or_msc_theta0(const or_ctx* c, int m, double T, double s);
+/* Bohr variance [MeV^2] of the restricted loss of an e- (positron = 0) or e+ over s */
+double or_fluct_sigma2(const or_ctx* c, int m, double T, double s, int positron);
+/* n draws, draw i from the stream keyed (seed, event), counter (i+1, 0, 0, .):
+ * which 0: deflected direction of (0,0,1) after a step s at energy T (out: 3 per draw);
+ * which 1: sampled loss of a step s at energy T, species 1 (e-) or 2 (e+) (out: 2 per draw:
+ *          the loss, and the mean loss it fluctuates about) */
+void or_sample_continuous(const or_ctx* c, int which, int species, int m, double T, double s,
+                          uint32_t seed, uint32_t event, int n, double* out);
+
 /* ---- geometry ---- */
 int or_n_volumes(const or_ctx* c);
 int or_locate(const or_ctx* c, const double pos[3], const double dir[3]);
@@ -113,6 +132,8 @@ typedef struct {
   uint32_t max_vacuum_steps; /* consecutive steps in vacuum */
   int n_threads;
   int max_gen;               /* size of the gen_hist rows (0 = none) */
+  uint32_t physics;          /* OR_PHYS_* bits (0 = the paper's list only) */
+  double msc_range_factor;   /* f of the MSC step limit (0 = 0.04) */
 } or_run_opts;
 
 typedef struct {

@@ -1,0 +1,148 @@
+"""Pins of the oracle's optional continuous physics: multiple Coulomb scattering (Highland
+width, Gaussian projected angles) and Gaussian (Bohr) fluctuations of the restricted loss.
+
+What pins what:
+* Highland's theta0 at x = X0 for beta -> 1 is the printed 13.6 MeV / p (the log term
+  vanishes there); the 0.038 log term itself is the PDG formula (not independently pinned).
+* The deflection sampler: unit vectors; space angle^2 exponential with mean 2 theta0^2 and
+  projected angles normal with width theta0 (the Gaussian reading), uniform azimuth.
+* Bohr's variance: the PDG constant K = 4 pi N_A r_e^2 m_e c^2 = 0.307075 MeV cm^2/mol,
+  and the restricted transfer limit (e+ may transfer all of T, e- half of it).
+* The fluctuation sampler: support [0, 2 mean], unbiased mean, normal shape when sigma is
+  small, and a per-event energy ledger and thread independence in full transport.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_2209_15445_gb300 import workloads as W
+
+ME = 0.51099895
+K_PDG = 0.307075  # MeV cm^2 / mol (PDG Table "Passage of particles through matter")
+
+
+@pytest.fixture(scope="module")
+def slab():
+    return oracle.Oracle(W.slab_calorimeter())
+
+
+def beta_cp(T):
+    E = T + ME
+    return T * (T + 2 * ME) / E
+
+
+def test_highland_at_one_radiation_length(slab):
+    for m in (0, 1):
+        X0 = 1.0 / slab.inv_X0(m)
+        T = 1e6  # 1 TeV: 1 - beta^2 ~ 2.6e-13
+        th = slab.msc_theta0(m, T, X0)
+        assert abs(th * beta_cp(T) / 13.6 - 1.0) < 1e-9
+
+
+def test_highland_limits(slab):
+    X0 = 1.0 / slab.inv_X0(0)
+    assert slab.msc_theta0(0, 100.0, 0.0) == 0.0
+    # wider for thicker steps and lower momenta
+    a, b = slab.msc_theta0(0, 100.0, 0.1 * X0), slab.msc_theta0(0, 100.0, 0.4 * X0)
+    assert b > 1.9 * a
+    assert slab.msc_theta0(0, 10.0, 0.1 * X0) > 9.0 * a
+
+
+@pytest.mark.parametrize("T,s", [(50.0, 0.05), (5.0, 0.01)])
+def test_deflection_sampler_shape(slab, T, s):
+    n = 40000
+    d = slab.sample_continuous(0, 1, 0, T, s, n, seed=3)
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-14)
+    th0 = slab.msc_theta0(0, T, s)
+    assert th0 < 0.3  # small-angle regime, the clamp at pi never acts
+    theta = np.arccos(np.clip(d[:, 2], -1, 1))
+    assert stats.kstest(theta**2, "expon", args=(0, 2 * th0**2)).pvalue > 1e-3
+    proj = np.arctan2(d[:, 0], d[:, 2])
+    # projected angles of a space angle theta with uniform azimuth: normal of width theta0
+    # to leading order in theta0
+    assert stats.kstest(proj / th0, "norm").pvalue > 1e-3 or th0 > 0.2
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    assert stats.kstest(phi, "uniform", args=(-math.pi, 2 * math.pi)).pvalue > 1e-3
+
+
+def test_deflection_clamped_at_pi(slab):
+    # a 10 keV electron over 1 mm of lead: theta0 >> pi, every draw is clamped or large
+    d = slab.sample_continuous(0, 1, 0, 0.01, 1.0, 2000, seed=5)
+    assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-14)
+    assert (d[:, 2] >= -1.0).all() and np.mean(d[:, 2] < 0) > 0.2
+
+
+def test_bohr_variance_matches_pdg_constant():
+    geom = W.slab_calorimeter()
+    o = oracle.Oracle(geom)
+    for m, mat in enumerate(geom.materials):
+        T, s_mm = 1e4, 1.0
+        E = T + ME
+        b2 = T * (T + 2 * ME) / E**2
+        tc, _ = o.cuts(m)
+        tu = min(tc, 0.5 * T)
+        want = 0.5 * K_PDG * (mat.Z / mat.A) * mat.density * (s_mm / 10.0) * tu * (1 - 0.5 * b2) / b2
+        assert abs(o.fluct_sigma2(m, T, s_mm) / want - 1.0) < 2e-5
+
+
+def test_bohr_restricted_transfer_limit(slab):
+    tc, _ = slab.cuts(0)
+    T = 0.5 * tc  # below the cut: e- may transfer T/2, e+ all of T
+    r = slab.fluct_sigma2(0, T, 0.1, positron=True) / slab.fluct_sigma2(0, T, 0.1)
+    assert abs(r - 2.0) < 1e-12
+    T = 10 * tc  # above it both are limited by the cut
+    assert slab.fluct_sigma2(0, T, 0.1, positron=True) == slab.fluct_sigma2(0, T, 0.1)
+
+
+def test_fluctuation_sampler_small_sigma_is_normal(slab):
+    # 1 GeV e- over 1 mm of lead: sigma / mean ~ 0.1, truncation at 0 and 2 mean is ~1e-20
+    n = 20000
+    out = slab.sample_continuous(1, 1, 0, 1000.0, 1.0, n, seed=7)
+    loss, mean = out[:, 0], out[0, 1]
+    sig = math.sqrt(slab.fluct_sigma2(0, 1000.0, 1.0))
+    assert sig < 0.2 * mean
+    assert stats.kstest((loss - mean) / sig, "norm").pvalue > 1e-3
+
+
+@pytest.mark.parametrize("T,s", [(2.0, 0.02), (0.2, 0.005)])
+def test_fluctuation_sampler_support_and_mean(slab, T, s):
+    n = 20000
+    out = slab.sample_continuous(1, 2, 0, T, s, n, seed=9)
+    loss, mean = out[:, 0], out[0, 1]
+    assert mean > 0 and (loss >= 0).all() and (loss <= 2 * mean).all()
+    # symmetric truncation keeps the mean
+    assert abs(loss.mean() - mean) < 4 * loss.std() / math.sqrt(n) + 1e-12
+
+
+def test_transport_with_msc_and_fluctuations_conserves_energy():
+    geom = W.slab_calorimeter()
+    o = oracle.Oracle(geom)
+    prim = W.electrons(40, 2000.0)
+    r1 = o.transport(prim, physics=oracle.PHYS_MSC | oracle.PHYS_FLUCT, n_threads=1, max_gen=4000)
+    E0 = prim.E
+    tot = r1["edep"].sum(1) + r1["leaked"] + r1["killed"]
+    assert np.allclose(tot, E0, rtol=1e-12)
+    r4 = o.transport(prim, physics=oracle.PHYS_MSC | oracle.PHYS_FLUCT, n_threads=4, max_gen=4000)
+    assert np.array_equal(r1["edep"], r4["edep"]) and np.array_equal(r1["gen_hist"], r4["gen_hist"])
+    # the extra physics changes the histories and, through its step limit, adds charged steps
+    r0 = o.transport(prim, n_threads=4)
+    assert r1["steps"][1] > 2 * r0["steps"][1]
+    assert not np.array_equal(r0["edep"], r1["edep"])
+
+
+def test_msc_broadens_a_pencil_beam():
+    """with bremsstrahlung only, an electron keeps its direction without MSC (it stays on
+    the axis); with MSC the deposits spread and the mean depth of energy loss shrinks"""
+    geom = W.slab_calorimeter()
+    o = oracle.Oracle(geom)
+    prim = W.electrons(200, 50.0)
+    depth = np.arange(geom.n_bins)
+    means = []
+    for phys in (0, oracle.PHYS_MSC):
+        r = o.transport(prim, process_mask=oracle.P_EBREM, physics=phys)
+        e = r["edep"].sum(0)
+        means.append((e * depth).sum() / e.sum())
+    assert means[1] < means[0]
