@@ -76,6 +76,9 @@ def args_parse():
     ap.add_argument("--genlog", default="", help="write the per-generation queue sizes of the last step here")
     ap.add_argument("--no-kernel-timing", action="store_true", help="no CUDA events around the transport kernels")
     ap.add_argument("--species-timing", action="store_true", help="also time each species kernel")
+    ap.add_argument("--physics", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="optional continuous physics: 1 multiple scattering, 2 loss fluctuations, 3 both "
+                         "(0: the paper's process list, the headline)")
     ap.add_argument("--fused", type=int, default=-1, choices=[-1, 0, 1],
                     help="1: one kernel per generation for all species; 0: concurrent species kernels; -1: tuned")
     return ap.parse_args()
@@ -140,7 +143,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def oracle_rate(n_events, energy, threads=None):
+def oracle_rate(n_events, energy, threads=None, physics=0):
     """FP64 oracle (as it stands) on n_events of the workload; returns (steps/s, steps, s, cores)."""
     import oracle
     from paper_2209_15445_gb300 import workloads as W
@@ -148,17 +151,17 @@ def oracle_rate(n_events, energy, threads=None):
     prim = W.electrons(n_events, energy, first_event=777000)
     cores = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
-    r = o.transport(prim, n_threads=cores)
+    r = o.transport(prim, n_threads=cores, physics=physics)
     dt = time.perf_counter() - t0
     steps = int(r["steps"].sum())
     return steps / dt, steps, dt, cores
 
 
-def cpu_baseline(energy, target_s=12.0):
-    rate, steps, dt, cores = oracle_rate(8, energy)
+def cpu_baseline(energy, target_s=12.0, physics=0):
+    rate, steps, dt, cores = oracle_rate(8, energy, physics=physics)
     per_event = steps / 8
     n = max(8, min(10000, int(target_s * rate / per_event)))
-    rate, steps, dt, cores = oracle_rate(n, energy)
+    rate, steps, dt, cores = oracle_rate(n, energy, physics=physics)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} of the 10,000 events ({steps} steps, {dt:.1f} s), FP64 C oracle on {cores} threads",
             "showers_per_s": n / dt}
@@ -242,6 +245,8 @@ def run_ours(a):
         launch_opts["graph_generations"] = a.graph
     if a.fused >= 0:
         launch_opts["fused"] = a.fused
+    if a.physics:
+        launch_opts["physics"] = a.physics
     tr = A.Transport(geom, precision=a.precision, arena_bytes=int(a.arena_gb * (1 << 30)),
                      flags=0 if a.no_kernel_timing else (A.FLAG_TIME_SPECIES if a.species_timing else A.FLAG_TIME_STEPS),
                      max_events=max(65536, n), **launch_opts)
@@ -325,7 +330,7 @@ def run_ours(a):
 
     base = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
-        base = cpu_baseline(E)
+        base = cpu_baseline(E, physics=a.physics)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": t_ms_max / a.steps, "higher_is_better": True,
@@ -335,6 +340,8 @@ def run_ours(a):
                            "graph_generations": tr.options.graph_generations,
                            "block": tr.options.block_size or 256,
                            "fused": int(tr.options.fused),
+                           "physics": {0: "paper process list", 1: "+ multiple scattering", 2: "+ loss fluctuations",
+                                       3: "+ multiple scattering + loss fluctuations"}[a.physics],
                            "blocks_per_sm": int(tr.options.blocks_per_sm),
                            "blocks_per_sm_species": list(tr.options.blocks_per_sm_species) if not a.bps else [a.bps] * 3,
                            "l2": "track queues (GBs) exceed L2; 256 MB buffer written between steps"},

@@ -56,6 +56,22 @@ extern "C" {
 #define ADEPT_P_POS_BREM (1u << 6)
 #define ADEPT_P_ANNIHILATION (1u << 7)
 
+/* Optional continuous physics (adept_options.physics). The paper's process list has
+ * neither; both are off by default.
+ *  ADEPT_PHYS_MSC: multiple Coulomb scattering of e+-: at the end of every charged step in
+ *    matter the direction turns by a space angle theta0 sqrt(-2 ln u) (two Gaussian
+ *    projected angles of Highland's width theta0 at the pre-step energy, PDG), at most pi,
+ *    with uniform azimuth; charged steps are limited to max(f R, 0.01 mm), f =
+ *    msc_range_factor.
+ *  ADEPT_PHYS_FLUCT: Gaussian fluctuations of the continuous (restricted) loss: Bohr's
+ *    variance for transfers up to min(production cut, largest transfer), the loss redrawn
+ *    into [0, 2 x mean] (at most 8 draws, then the mean), for tracks that survive the mean
+ *    loss of a step shorter than their range.
+ * Their random numbers come from counter blocks 0x40000000 (deflection) and 0x40000001.. of
+ * the step's stream, apart from the interaction sampling. */
+#define ADEPT_PHYS_MSC (1u << 0)
+#define ADEPT_PHYS_FLUCT (1u << 1)
+
 typedef struct adept_ctx adept_ctx; /* opaque, library-owned */
 
 /* Calorimeter geometry. kind 0: a stack of n_layers identical layers along +z starting
@@ -116,6 +132,8 @@ typedef struct {
                                  and a close kernel follows them; 1: one kernel per generation
                                  for all three species, whose last block closes the generation;
                                  blocks_per_sm picks its variant (2 or 3 split, 1 or 2 FP64) [0] */
+  uint32_t physics;           /* ADEPT_PHYS_* bits [0] */
+  double msc_range_factor;    /* f of the multiple-scattering step limit [0.04] */
 } adept_options;
 
 /* adept_options.flags: time every generation (its three transport kernels, from the fork to
@@ -252,6 +270,13 @@ int adept_probe_distance(adept_ctx* ctx, int32_t prec, const double* host_pos,
                          const int32_t* host_charge, size_t n, double* host_s, int32_t* host_next);
 int adept_probe_sample(adept_ctx* ctx, int32_t which, int32_t m, int32_t prec, double E,
                        uint32_t event, size_t n, double* host_out);
+/*  - continuous: n draws of the optional along-step physics in material m at kinetic energy
+ *    T over path s, stream i keyed (seed, event) with track id i+1 at step 0:
+ *    which 0, the multiple-scattering deflection of the direction (0,0,1): 3 doubles per
+ *    draw; which 1, the fluctuated loss of an e- (species 1) or e+ (species 2) and the mean
+ *    loss it fluctuates about: 2 doubles per draw. */
+int adept_probe_continuous(adept_ctx* ctx, int32_t which, int32_t species, int32_t m, int32_t prec,
+                           double T, double s, uint32_t event, size_t n, double* host_out);
 
 /* Table build without any allocation, for callers that cannot allocate device memory:
  * code that runs under a host framework which owns every device allocation (a fixed

@@ -25,6 +25,9 @@ _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ESTATE: "ESTATE", ECUDA: "ECUDA", 
 FLAG_TIME_STEPS = 1
 FLAG_TIME_SPECIES = 4
 FLAG_STEP_HISTOGRAM = 8
+# optional continuous physics (adept_options.physics)
+PHYS_MSC = 1
+PHYS_FLUCT = 2
 P_COMPTON, P_CONVERSION, P_PHOTO, P_E_IONI, P_E_BREM, P_POS_IONI, P_POS_BREM, P_ANNIH = (1 << i for i in range(8))
 NNODE = 289
 
@@ -56,7 +59,8 @@ class adept_options(C.Structure):
                 ("max_steps", C.c_uint32), ("max_vacuum_steps", C.c_uint32), ("max_events", C.c_uint32),
                 ("max_generation_log", C.c_uint32), ("track_capacity", C.c_uint64),
                 ("tracks_per_MeV", C.c_double), ("flags", C.c_int32),
-                ("blocks_per_sm_species", C.c_int32 * 3), ("fused", C.c_int32)]
+                ("blocks_per_sm_species", C.c_int32 * 3), ("fused", C.c_int32),
+                ("physics", C.c_uint32), ("msc_range_factor", C.c_double)]
 
 
 TRACK_DTYPE = np.dtype([("pdg", "<i4"), ("pad0", "<i4"), ("E", "<f8"), ("pos", "<f8", 3), ("dir", "<f8", 3),
@@ -120,6 +124,7 @@ def load(path: str = LIB_PATH):
             "adept_probe_inverse_range": [vp, i32, i32, i32, dp, sz, dp],
             "adept_probe_distance": [vp, i32, dp, dp, i32p, dp, i32p, sz, dp, i32p],
             "adept_probe_sample": [vp, i32, i32, i32, C.c_double, u32, sz, dp],
+            "adept_probe_continuous": [vp, i32, i32, i32, i32, C.c_double, C.c_double, u32, sz, dp],
             "adept_build_tables_noalloc": [C.POINTER(adept_material), i32, C.c_double, vp, vp, vp],
         }
         for name, args in sig.items():
@@ -271,6 +276,12 @@ def adept_build_tables_noalloc(materials, range_cut_mm, dev_tables_ptr, dev_cuts
 def adept_probe_sample(h, which, m, prec, E, event, n):
     out = np.zeros((n, 12))
     rc = load().adept_probe_sample(h, which, m, prec, E, event, n, _dp(out))
+    return rc, out
+
+
+def adept_probe_continuous(h, which, species, m, prec, T, s, event, n):
+    out = np.zeros((n, 3 if which == 0 else 2))
+    rc = load().adept_probe_continuous(h, which, species, m, prec, T, s, event, n, _dp(out))
     return rc, out
 
 

@@ -265,6 +265,9 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (o.flags & ~(ADEPT_FLAG_TIME_STEPS | ADEPT_FLAG_TIME_SPECIES | ADEPT_FLAG_STEP_HISTOGRAM)) return ADEPT_EINVAL;
   if (o.fused != 0 && o.fused != 1) return ADEPT_EINVAL;
   if (o.fused && (o.flags & ADEPT_FLAG_TIME_SPECIES)) return ADEPT_EINVAL;  // needs separate species kernels
+  if (o.physics & ~(ADEPT_PHYS_MSC | ADEPT_PHYS_FLUCT)) return ADEPT_EINVAL;
+  if (o.msc_range_factor < 0.0 || !(o.msc_range_factor < 1e30)) return ADEPT_EINVAL;
+  if (o.msc_range_factor == 0.0) o.msc_range_factor = 0.04;
   if (o.block_size == 0) o.block_size = 256;
   if (o.block_size < 32 || o.block_size > 256 || (o.block_size & 31)) return ADEPT_EINVAL;
   if (o.graph_generations < -1 || o.graph_generations > 1024) return ADEPT_EINVAL;
@@ -345,6 +348,8 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   P.tcut = cuts->tracking_cut_MeV;
   P.seed = o.seed; P.process_mask = o.process_mask; P.max_steps = o.max_steps; P.max_vac = o.max_vacuum_steps;
   P.steplen = (o.flags & ADEPT_FLAG_STEP_HISTOGRAM) ? steplen : nullptr;
+  P.physics = o.physics;
+  P.msc_f = o.msc_range_factor;
   c->steplen = steplen;
   // device state
   adept_ctx* c_ = cp;
@@ -1024,6 +1029,22 @@ extern "C" int adept_probe_sample(adept_ctx* c, int32_t which, int32_t m, int32_
   double* dout = reinterpret_cast<double*>(c->probe);
   CK(launch_probe_sample(c->P, which, m, prec, E, event, (int)n, dout, c->stream));
   CK(cudaMemcpyAsync(host_out, dout, 96 * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ADEPT_OK;
+}
+
+extern "C" int adept_probe_continuous(adept_ctx* c, int32_t which, int32_t species, int32_t m, int32_t prec, double T,
+                                      double s, uint32_t event, size_t n, double* host_out) {
+  if (!c || which < 0 || which > 1 || (species != 1 && species != 2) || m < 0 || m >= c->n_mat ||
+      (prec != 0 && prec != 1) || (n && !host_out) || !(T >= 1e-3 && T <= 1e6) || !(s >= 0.0))
+    return ADEPT_EINVAL;
+  if (c->mats[m].Z <= 0) return fail(c, ADEPT_EINVAL, "material %d is vacuum", m);
+  if (!c->built) return fail(c, ADEPT_ESTATE, "tables not built");
+  const size_t per = which == 0 ? 24 : 16;
+  if (n > c->probe_bytes / per) return fail(c, ADEPT_EINVAL, "at most %zu draws per call", c->probe_bytes / per);
+  double* dout = reinterpret_cast<double*>(c->probe);
+  CK(launch_probe_continuous(c->P, which, species, m, prec, T, s, event, (int)n, dout, c->stream));
+  CK(cudaMemcpyAsync(host_out, dout, per * n, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return ADEPT_OK;
 }

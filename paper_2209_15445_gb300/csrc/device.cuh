@@ -152,6 +152,12 @@ template <> struct Stream<double> {
     *u0 = u01d(r.a, r.b);
     *u1 = u01d(r.c, r.d);
   }
+  // the two uniforms of counter block b, outside the sampling sequence
+  __device__ __forceinline__ void pair(uint32_t b, double* ua, double* ub) const {
+    const U4 r = philox(U4{c0, c1, c2, b}, k0, k1);
+    *ua = u01d(r.a, r.b);
+    *ub = u01d(r.c, r.d);
+  }
   __device__ __forceinline__ double next() {
     if (used >= 4) { w = philox(U4{c0, c1, c2, ++blk}, k0, k1); used = 0; }
     const double u = used == 0 ? u01d(w.a, w.b) : u01d(w.c, w.d);
@@ -169,6 +175,11 @@ template <> struct Stream<float> {
     const U4 r = philox(U4{c0, c1, c2, 0u}, k0, k1);
     *u0 = u01f(r.a);
     *u1 = u01f(r.c);
+  }
+  __device__ __forceinline__ void pair(uint32_t b, float* ua, float* ub) const {
+    const U4 r = philox(U4{c0, c1, c2, b}, k0, k1);
+    *ua = u01f(r.a);
+    *ub = u01f(r.c);
   }
   __device__ __forceinline__ float next() {
     if (used >= 2) {
@@ -509,6 +520,65 @@ __device__ void annihilate(Stream<R>& st, double T, const R u[3], Ixn<R>& r) {
   R x = pp * u[0] - E1f * r.d[0][0], y = pp * u[1] - E1f * r.d[0][1], z = pp * u[2] - E1f * r.d[0][2];
   unit<R>(&x, &y, &z);
   r.d[1][0] = x; r.d[1][1] = y; r.d[1][2] = z;
+}
+
+// ---------------------------------------------------------------- optional continuous physics
+// Counter blocks of the along-step draws (phase A): they never meet the model-sampling
+// blocks 1, 2, ... of phase B, nor the child-id blocks with the top bit set.
+constexpr uint32_t kMscBlock = 0x40000000u;
+constexpr uint32_t kFluctBlock = 0x40000001u;
+constexpr double kTwoPiRe2Me = 2.0 * kPi * kRe * kRe * kMe;  // MeV mm^2
+
+// Highland's width of the projected multiple-scattering angle (PDG, passage of particles
+// through matter): 13.6 MeV / (beta c p) sqrt(x/X0) (1 + 0.038 ln(x / (X0 beta^2))) for a
+// unit charge at kinetic energy T over path s; the bracket is clamped at 0.
+template <class R>
+__device__ __forceinline__ R msc_theta0(R T, R inv_x0, R s) {
+  const R E = T + (R)kMe, pc2 = T * (T + (R)(2.0 * kMe));
+  const R beta2 = M<R>::fdiv(pc2, E * E), bcp = M<R>::fdiv(pc2, E);
+  const R x = s * inv_x0;
+  if (!(x > (R)0)) return (R)0;
+  R br = (R)1 + (R)0.038 * M<R>::flog(M<R>::fdiv(x, beta2));
+  br = br < (R)0 ? (R)0 : br;
+  return M<R>::fdiv((R)13.6, bcp) * M<R>::sqrt(x) * br;
+}
+
+// Bohr's variance of the loss over s to transfers up to min(Tc, largest transfer): T/2 for
+// e-, T for e+. xi_coef = 2 pi r_e^2 m c^2 n_el of the material.
+template <class R>
+__device__ __forceinline__ R fluct_sigma2(R T, R xi_coef, R Tc, R s, bool positron) {
+  const R E = T + (R)kMe, beta2 = M<R>::fdiv(T * (T + (R)(2.0 * kMe)), E * E);
+  const R tmax = positron ? T : (R)0.5 * T;
+  const R tu = Tc < tmax ? Tc : tmax;
+  return M<R>::fdiv(xi_coef * s * tu * ((R)1 - (R)0.5 * beta2), beta2);
+}
+
+// Multiple scattering at the end of a step: space angle theta0 sqrt(-2 ln ua) (two
+// Gaussian projected angles of width theta0), at most pi, azimuth 2 pi ub.
+template <class R>
+__device__ __forceinline__ void msc_deflect(const Stream<R>& st, R theta0, R u[3]) {
+  R ua, ub;
+  st.pair(kMscBlock, &ua, &ub);
+  R th = theta0 * M<R>::sqrt((R)-2 * M<R>::flog(ua));
+  th = th > (R)kPi ? (R)kPi : th;
+  R o0, o1, o2;
+  rotate_to<R>(u[0], u[1], u[2], M<R>::fcos(th), (R)(2.0 * kPi) * ub, &o0, &o1, &o2);
+  unit<R>(&o0, &o1, &o2);
+  u[0] = o0; u[1] = o1; u[2] = o2;
+}
+
+// Gaussian loss about the mean, redrawn at most 8 times (then the mean) until it lies in
+// [0, 2 mean]; one Box-Muller normal per counter block
+template <class R>
+__device__ __forceinline__ double fluct_loss(const Stream<R>& st, double mean, R sigma) {
+  for (uint32_t i = 0; i < 8; ++i) {
+    R ua, ub;
+    st.pair(kFluctBlock + i, &ua, &ub);
+    const R g = M<R>::sqrt((R)-2 * M<R>::flog(ua)) * M<R>::fcos((R)(2.0 * kPi) * ub);
+    const double d = mean + to_d<R>(sigma * g);
+    if (d >= 0.0 && d <= 2.0 * mean) return d;
+  }
+  return mean;
 }
 
 template <class R>

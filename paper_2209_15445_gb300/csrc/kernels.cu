@@ -473,4 +473,41 @@ cudaError_t launch_probe_sample(const Params& P, int which, int m, int prec, dou
   return cudaGetLastError();
 }
 
+template <class R>
+__global__ void k_probe_continuous(Params P, int which, int species, int m, double T, double s, uint32_t event, int n,
+                                   double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Stream<R> st(P.seed, event, (unsigned long long)(i + 1), 0u);
+  const MatDev& md = P.mat[m];
+  if (which == 0) {
+    R u[3] = {(R)0, (R)0, (R)1};
+    msc_deflect<R>(st, msc_theta0<R>((R)T, (R)md.inv_x0, (R)s), u);
+    out[3 * (size_t)i] = u[0]; out[3 * (size_t)i + 1] = u[1]; out[3 * (size_t)i + 2] = u[2];
+    return;
+  }
+  // the mean loss as in the step: through the range table of the species
+  int bin;
+  R tt;
+  grid_pos<R>(T, &bin, &tt);
+  const auto* rec = (species == 2 ? tab_p<R>(P.tab) + ((size_t)m * kNNode + bin) * kNTabP
+                                  : tab_e<R>(P.tab) + ((size_t)m * kNNode + bin) * kNTabE);
+  const R Rr = lerp_rec<R>(rec, 1, tt);
+  R Epr = 0;
+  if ((R)s < Rr) Epr = inverse_range<R>(range_nodes<R>(P.tab, species == 2) + (size_t)m * kNNode, Rr - (R)s, bin + 1);
+  const double Ep = (Epr > (R)T) ? T : to_d<R>(Epr);
+  const R xi = (R)(kTwoPiRe2Me * md.n_el);
+  const R sig = M<R>::sqrt(fluct_sigma2<R>((R)T, xi, (R)P.tab.Tc[m], (R)s, species == 2));
+  out[2 * (size_t)i] = fluct_loss<R>(st, T - Ep, sig);
+  out[2 * (size_t)i + 1] = T - Ep;
+}
+
+cudaError_t launch_probe_continuous(const Params& P, int which, int species, int m, int prec, double T, double s,
+                                    uint32_t event, int n, double* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (prec) k_probe_continuous<float><<<(n + 127) / 128, 128, 0, st>>>(P, which, species, m, T, s, event, n, out);
+  else k_probe_continuous<double><<<(n + 127) / 128, 128, 0, st>>>(P, which, species, m, T, s, event, n, out);
+  return cudaGetLastError();
+}
+
 }  // namespace adept

@@ -108,6 +108,8 @@ struct Params {
   double tcut;
   uint32_t seed, process_mask, max_steps, max_vac;
   unsigned long long* steplen;  // [3][64] step-length histogram (log2 bins), or null
+  uint32_t physics;     // ADEPT_PHYS_* bits: multiple scattering, loss fluctuations
+  double msc_f;         // multiple-scattering step limit: s <= max(msc_f R, 0.01 mm)
 };
 
 // device view of one submitted particle; same layout as adept_track in adept.h
@@ -152,6 +154,8 @@ cudaError_t launch_probe_distance(const Params& P, int prec, const double* pos, 
 cudaError_t launch_probe_sample(const Params& P, int which, int m, int prec, double E, uint32_t event,
                                 int n, double* out, cudaStream_t st);
 int transport_max_blocks_per_sm(int precision, int species, int minb, int block);
+cudaError_t launch_probe_continuous(const Params& P, int which, int species, int m, int prec, double T, double s,
+                                    uint32_t event, int n, double* out, cudaStream_t st);
 // one kernel per generation for all species; its last block closes the generation
 cudaError_t launch_fused_generation(const Params& P, int precision, int minb, int grid, int block, cudaStream_t st);
 int fused_max_blocks_per_sm(int precision, int minb, int block);

@@ -159,8 +159,14 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
   const R stot = sg0 + sg1 + sg2;
   // S3/S4: sampled interaction length and the range-based step limit
   R s_phys = stot > (R)0 ? M<R>::fdiv(-M<R>::flog(u0), stot) : M<R>::big();
+  const bool msc = (P.physics & 1u) != 0, fluct = (P.physics & 2u) != 0;
   if (q != 0 && m >= 0) {
-    const R smax = (Rr <= (R)kRhoF) ? Rr : ((R)kAlphaR * Rr > (R)kRhoF ? (R)kAlphaR * Rr : (R)kRhoF);
+    R smax = (Rr <= (R)kRhoF) ? Rr : ((R)kAlphaR * Rr > (R)kRhoF ? (R)kAlphaR * Rr : (R)kRhoF);
+    if (msc) {  // multiple-scattering step limit
+      const R fR = (R)P.msc_f * Rr;
+      const R sm = fR > (R)0.01 ? fR : (R)0.01;
+      if (sm < smax) smax = sm;
+    }
     if (smax < s_phys) s_phys = smax;
   }
   // S5/S6: distance to the boundary along the straight line or helix
@@ -186,19 +192,27 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
     atomicAdd(P.steplen + 64 * S + b, 1ull);
   }
 
-  // S7: continuous loss by inverting the range table
+  // S7: continuous loss by inverting the range table; optionally a Gaussian loss about
+  // that mean for a track that survives the mean loss
   if (q != 0 && m >= 0) {
     R Epr = 0;
     if (s < Rr) Epr = inverse_range<R>(range_nodes<R>(P.tab, S == 2) + (size_t)m * kNNode, Rr - s, bin + 1);
-    const double Ep = (Epr > Er) ? t.E : to_d<R>(Epr);
+    double Ep = (Epr > Er) ? t.E : to_d<R>(Epr);
+    if (fluct && s < Rr && Ep >= P.tcut) {
+      const R xi = (R)(kTwoPiRe2Me * __ldg(&P.mat[m].n_el));
+      const R sig = M<R>::sqrt(fluct_sigma2<R>(Er, xi, (R)__ldg(P.tab.Tc + m), s, S == 2));
+      Ep = t.E - fluct_loss<R>(rs, t.E - Ep, sig);
+    }
     dep += t.E - Ep;
     t.E = Ep;
-    if (Epr < tcut) {
+    if (to_r<R>(Ep) < tcut) {
       dep += t.E;
       t.E = 0.0;
       if (S == 2) annihilate_at_rest<R>(rs, sec);
       return kDead;
     }
+    // optional multiple scattering: the direction at the end of the step
+    if (msc && s > (R)0) msc_deflect<R>(rs, msc_theta0<R>(Er, (R)__ldg(&P.mat[m].inv_x0), s), t.u);
   }
   // S8: boundary crossing
   if (boundary) {
