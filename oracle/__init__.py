@@ -48,7 +48,8 @@ def build(force: bool = False) -> str:
 class _RunOpts(C.Structure):
     _fields_ = [("seed", C.c_uint32), ("process_mask", C.c_uint32), ("max_steps", C.c_uint32),
                 ("max_vacuum_steps", C.c_uint32), ("n_threads", C.c_int), ("max_gen", C.c_int),
-                ("physics", C.c_uint32), ("msc_range_factor", C.c_double)]
+                ("physics", C.c_uint32), ("msc_range_factor", C.c_double),
+                ("field_max_iter", C.c_int), ("delta_chord", C.c_double), ("delta_int", C.c_double)]
 
 
 class _Result(C.Structure):
@@ -91,6 +92,8 @@ def lib():
             L.or_sample.argtypes = [p, i, i, d, u32, u32, i, dp]
             L.or_sample_continuous.argtypes = [p, i, i, i, d, d, u32, u32, i, dp]
             L.or_msc_theta0.argtypes = [p, i, d, d]; L.or_msc_theta0.restype = d
+            L.or_chord_step.argtypes = [p, d, i, d, i, d, d, dp, dp, i, ip, dp, ip]
+            L.or_chord_step.restype = i
             L.or_fluct_sigma2.argtypes = [p, i, d, d, i]; L.or_fluct_sigma2.restype = d
             L.or_n_volumes.argtypes = [p]; L.or_n_volumes.restype = i
             L.or_n_bins.argtypes = [p]; L.or_n_bins.restype = i
@@ -201,6 +204,14 @@ class Oracle:
         return out
 
     def msc_theta0(self, m, T, s): return lib().or_msc_theta0(self.h, m, T, s)
+
+    def chord_step(self, T, q, s_phys, max_iter, pos, d, vol, delta_chord=0.25, delta_int=0.001):
+        """(status, position, direction, next, path, iterations) of one chord-propagated step"""
+        pos = np.array(pos, np.float64); d = np.array(d, np.float64)
+        nx, sd, it = C.c_int(vol), C.c_double(), C.c_int()
+        rc = lib().or_chord_step(self.h, T, q, s_phys, max_iter, delta_chord, delta_int, _dp(pos), _dp(d), vol,
+                                 C.byref(nx), C.byref(sd), C.byref(it))
+        return rc, pos, d, nx.value, sd.value, it.value
     def fluct_sigma2(self, m, T, s, positron=False): return lib().or_fluct_sigma2(self.h, m, T, s, int(positron))
 
     def sample_continuous(self, which, species, m, T, s, n, seed=1, event=0) -> np.ndarray:
@@ -227,7 +238,7 @@ class Oracle:
 
     def transport(self, prim, seed=1, process_mask=0, max_steps=100000, max_vacuum_steps=1000,
                   n_threads=None, max_gen=0, steplen=False, event_slot=None, n_events=None,
-                  physics=0, msc_range_factor=0.0):
+                  physics=0, msc_range_factor=0.0, field_max_iter=0, delta_chord=0.0, delta_int=0.0):
         """Transport primaries; tracks with the same event number form one event (slot
         order = first appearance) unless event_slot is given."""
         n = len(prim)
@@ -249,7 +260,8 @@ class Oracle:
         res.gen_hist = gen.ctypes.data_as(C.POINTER(C.c_uint64)) if max_gen > 0 else None
         res.steplen_hist = sl.ctypes.data_as(C.POINTER(C.c_uint64)) if steplen else None
         o = _RunOpts(seed, process_mask, max_steps, max_vacuum_steps,
-                     n_threads or os.cpu_count() or 1, max_gen, physics, msc_range_factor)
+                     n_threads or os.cpu_count() or 1, max_gen, physics, msc_range_factor, field_max_iter,
+                     delta_chord, delta_int)
         pdg = np.ascontiguousarray(prim.pdg, np.int32)
         E = np.ascontiguousarray(prim.E, np.float64)
         pos = np.ascontiguousarray(prim.pos, np.float64)

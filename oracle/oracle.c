@@ -696,6 +696,121 @@ double or_helix_distance(const or_ctx* c, double T, int q, const double p[3], co
   return s;
 }
 
+/* ------------------------------------------------------------------ chord propagation */
+/* is p inside (or on the boundary of) volume vol */
+static int inside_volume(const or_ctx* c, const double p[3], int vol) {
+  if (c->kind == 0) {
+    return p[2] >= c->bnd[vol] && p[2] <= c->bnd[vol + 1] && fabs(p[0]) <= c->half_xy &&
+           fabs(p[1]) <= c->half_xy;
+  }
+  const double r2 = p[0] * p[0] + p[1] * p[1];
+  if (fabs(p[2]) > c->half_z) return 0;
+  if (r2 > c->bnd[vol] * c->bnd[vol]) return 0;
+  return vol == 0 || r2 >= c->bnd[vol - 1] * c->bnd[vol - 1];
+}
+
+/* the point and direction at path s along the helix from (p0, u0) */
+static void helix_at(double B, double T, int q, const double p0[3], const double u0[3], double s, double p[3],
+                     double u[3]) {
+  memcpy(p, p0, 3 * sizeof(double));
+  memcpy(u, u0, 3 * sizeof(double));
+  or_helix_move(B, T, q, s, p, u);
+}
+
+int or_chord_step(const or_ctx* c, double T, int q, double s_phys, int max_iter, double delta_chord,
+                  double delta_int, double p[3], double u[3], int vol, int* next, double* s_done,
+                  int* iters) {
+  const double B = c->field_T;
+  helix_t H;
+  helix_setup(B, T, q, u, p, &H);
+  *iters = 0;
+  if (H.straight) { /* no curvature: one straight segment */
+    *iters = 1;
+    const double sg = or_distance(c, p, u, vol, next);
+    const double s = sg <= s_phys ? sg : s_phys;
+    p[0] += s * u[0]; p[1] += s * u[1]; p[2] += s * u[2];
+    *s_done = s;
+    return sg <= s_phys ? 1 : 0;
+  }
+  double ps[3], us[3], tmp[3];                           /* the state at the step's start */
+  memcpy(ps, p, sizeof(ps));
+  memcpy(us, u, sizeof(us));
+  const double kappa = H.uT * H.kpath;                   /* |du/ds| of the helix */
+  const double lmax = sqrt(8.0 * delta_chord / kappa);   /* sagitta kappa l^2 / 8 <= delta_chord */
+  const double lint = sqrt(8.0 * delta_int / kappa);
+  double s0 = 0.0, P0[3];
+  memcpy(P0, ps, sizeof(P0));
+  for (;;) {
+    if (++*iters > max_iter) return 2;
+    const double ell = (s_phys - s0 < lmax) ? s_phys - s0 : lmax;
+    double P1[3], U1[3];
+    helix_at(B, T, q, ps, us, s0 + ell, P1, U1);
+    double d[3] = {P1[0] - P0[0], P1[1] - P0[1], P1[2] - P0[2]};
+    const double L = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    int nx = vol;
+    double sb = kInf;
+    if (L > 0.0) {
+      d[0] /= L; d[1] /= L; d[2] /= L;
+      sb = or_distance(c, P0, d, vol, &nx);
+    }
+    /* a segment that meets the boundary: look for a curve point outside the volume, at the
+     * segment's end or where the segment meets the boundary */
+    double hi = -1.0;
+    if (sb < L) {
+      if (!inside_volume(c, P1, vol)) {
+        hi = s0 + ell;
+      } else {
+        const double sc = s0 + ell * (sb / L);
+        double Pc[3];
+        helix_at(B, T, q, ps, us, sc, Pc, tmp);
+        if (!inside_volume(c, Pc, vol)) hi = sc;
+      }
+    }
+    if (hi < 0.0) { /* no crossing on this segment */
+      s0 += ell;
+      memcpy(P0, P1, sizeof(P0));
+      if (s0 >= s_phys) {
+        memcpy(p, P1, sizeof(P1));
+        memcpy(u, U1, sizeof(U1));
+        *s_done = s_phys;
+        return 0;
+      }
+      continue;
+    }
+    /* refine: bisection between an inside (lo) and an outside (hi) point of the curve until
+     * the chord between them has a sagitta of at most delta_int */
+    double lo = s0, Plo[3], Phi[3];
+    memcpy(Plo, P0, sizeof(Plo));
+    helix_at(B, T, q, ps, us, hi, Phi, tmp);
+    while (hi - lo > lint) {
+      if (++*iters > max_iter) return 2;
+      const double mid = 0.5 * (lo + hi);
+      double Pm[3];
+      helix_at(B, T, q, ps, us, mid, Pm, tmp);
+      if (inside_volume(c, Pm, vol)) { lo = mid; memcpy(Plo, Pm, sizeof(Plo)); }
+      else { hi = mid; memcpy(Phi, Pm, sizeof(Phi)); }
+    }
+    /* the crossing lies on that chord; the direction is the curve's at the matching path */
+    double e[3] = {Phi[0] - Plo[0], Phi[1] - Plo[1], Phi[2] - Plo[2]};
+    const double Le = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    double sx = hi;
+    if (Le > 0.0) {
+      e[0] /= Le; e[1] /= Le; e[2] /= Le;
+      double sbe = or_distance(c, Plo, e, vol, &nx);
+      if (sbe > Le) sbe = Le;
+      sx = lo + (sbe / Le) * (hi - lo);
+      p[0] = Plo[0] + sbe * e[0]; p[1] = Plo[1] + sbe * e[1]; p[2] = Plo[2] + sbe * e[2];
+    } else {
+      memcpy(p, Phi, sizeof(Phi));
+    }
+    double Px[3];
+    helix_at(B, T, q, ps, us, sx, Px, u);
+    *next = nx;
+    *s_done = sx;
+    return 1;
+  }
+}
+
 /* ------------------------------------------------------------------ kinematics helpers */
 /* rotate the local direction (sin t cos f, sin t sin f, cos t) from the frame whose z axis
  * is u into the global frame */
@@ -1297,17 +1412,33 @@ static int step_track(ev_t* e, trk_t* t, stack_t_* st) {
 
   int next;
   const int field = (q != 0 && c->field_T != 0.0);
-  const double s_geom = field ? or_helix_distance(c, t->T, q, t->x, t->u, t->vol, &next)
-                              : or_distance(c, t->x, t->u, t->vol, &next);
-  const int boundary = (s_geom <= s_phys);
-  const double s = boundary ? s_geom : s_phys;
-  record(e, t, s);
-
-  /* move */
-  if (field) {
-    or_helix_move(c->field_T, t->T, q, s, t->x, t->u);
+  int boundary;
+  double s;
+  if (field && o->field_max_iter > 0) {
+    /* chord propagation (paper Sec. 2.3): a step whose integration does not finish within
+     * the iteration cap is killed and its energy accounted */
+    double sd;
+    int iters;
+    const int rc = or_chord_step(c, t->T, q, s_phys, o->field_max_iter,
+                                 o->delta_chord > 0.0 ? o->delta_chord : 0.25,
+                                 o->delta_int > 0.0 ? o->delta_int : 0.001, t->x, t->u, t->vol, &next, &sd,
+                                 &iters);
+    if (rc == 2) { record(e, t, 0.0); e->killed += t->T + rest; return 0; }
+    boundary = (rc == 1);
+    s = sd;
+    record(e, t, s);
   } else {
-    t->x[0] += s * t->u[0]; t->x[1] += s * t->u[1]; t->x[2] += s * t->u[2];
+    const double s_geom = field ? or_helix_distance(c, t->T, q, t->x, t->u, t->vol, &next)
+                                : or_distance(c, t->x, t->u, t->vol, &next);
+    boundary = (s_geom <= s_phys);
+    s = boundary ? s_geom : s_phys;
+    record(e, t, s);
+    /* move */
+    if (field) {
+      or_helix_move(c->field_T, t->T, q, s, t->x, t->u);
+    } else {
+      t->x[0] += s * t->u[0]; t->x[1] += s * t->u[1]; t->x[2] += s * t->u[2];
+    }
   }
   if (boundary && c->kind == 0 && next >= 0) {
     /* a crossing into another slab is through a z plane: land exactly on it */

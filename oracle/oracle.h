@@ -124,6 +124,17 @@ void or_helix_move(double field_T, double T, int charge, double s, double pos[3]
 double or_helix_distance(const or_ctx* c, double T, int charge, const double pos[3],
                          const double dir[3], int vol, int* next);
 
+/* chord propagation in the field (paper Sec. 2.3): the path of a charged track is
+ * followed in linear segments whose sagitta is at most delta_chord; a segment that meets
+ * the boundary of the volume is refined until the crossing is within delta_int of the
+ * curve. Each segment and each refinement is one iteration; a step needing more than
+ * max_iter does not finish. Starting at p/u in volume vol with a physics step s_phys:
+ * returns 0 (reached s_phys), 1 (crossed into *next, -1 = left the world) or 2 (cap hit,
+ * p/u unchanged); *s_done = path length, *iters = iterations used. */
+int or_chord_step(const or_ctx* c, double T, int q, double s_phys, int max_iter, double delta_chord,
+                  double delta_int, double p[3], double u[3], int vol, int* next, double* s_done,
+                  int* iters);
+
 /* ---- transport ---- */
 typedef struct {
   uint32_t seed;
@@ -134,6 +145,9 @@ typedef struct {
   int max_gen;               /* size of the gen_hist rows (0 = none) */
   uint32_t physics;          /* OR_PHYS_* bits (0 = the paper's list only) */
   double msc_range_factor;   /* f of the MSC step limit (0 = 0.04) */
+  int field_max_iter;        /* 0: analytic helix; N > 0: chord propagation, at most N iterations */
+  double delta_chord;        /* chord sagitta limit [mm] (0 = 0.25) */
+  double delta_int;          /* intersection accuracy [mm] (0 = 0.001) */
 } or_run_opts;
 
 typedef struct {
