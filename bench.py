@@ -79,6 +79,8 @@ def args_parse():
     ap.add_argument("--physics", type=int, default=0, choices=[0, 1, 2, 3],
                     help="optional continuous physics: 1 multiple scattering, 2 loss fluctuations, 3 both "
                          "(0: the paper's process list, the headline)")
+    ap.add_argument("--field-iter", type=int, default=0,
+                    help="c3/c4: chord propagation in the field with this iteration cap (0: analytic helix)")
     ap.add_argument("--fused", type=int, default=-1, choices=[-1, 0, 1],
                     help="1: one kernel per generation for all species; 0: concurrent species kernels; -1: tuned")
     return ap.parse_args()
@@ -403,6 +405,8 @@ def run_study(a):
             name = "100,000 e-/gamma 1-50 GeV, |eta|<1.5, 20-layer barrel, 3.8 T; split, batched in 100 requests"
             chunks, arena = 100, 40 << 30
         fo = {"fused": a.fused} if a.fused >= 0 else {}
+        if a.field_iter:
+            fo["field_max_iterations"] = a.field_iter
         tr = A.Transport(geom, precision=a.precision, field_T=field, arena_bytes=arena, graph_generations=a.graph,
                          flags=A.FLAG_TIME_STEPS if a.fused == 1 else A.FLAG_TIME_SPECIES, max_events=200000,
                          tracks_per_MeV=0.1, **fo)
@@ -413,16 +417,23 @@ def run_study(a):
         def once():
             ids = [tr.submit(x) for x in arrs]
             tr.transport()
+            k = 0.0
             for rid, pp in zip(ids, parts):
-                tr.result(rid, len(pp))
+                k += tr.result(rid, len(pp))[1].killed_MeV
+            return k
         once()
         s0 = tr.stats(); torch.cuda.synchronize(); t0 = time.perf_counter()
+        killed = 0.0
         for _ in range(a.steps):
-            once()
+            killed += once()
         torch.cuda.synchronize(); dt = time.perf_counter() - t0; s1 = tr.stats()
         st = sum(s1.steps) - sum(s0.steps)
         print(json.dumps(_line(a, name, st / dt, dt / a.steps,
                                {"showers_per_s": n * a.steps / dt, "steps_per_primary": st / (n * a.steps),
+                                "field": f"chords, at most {a.field_iter} iterations per step" if a.field_iter
+                                else "analytic helix",
+                                "killed_fraction": killed / (a.steps * float((prim.E + np.where(prim.pdg == -11,
+                                                                                                 2 * 0.51099895, 0.0)).sum())),
                                 "species_ms_per_step": [round((s1.species_ms[k] - s0.species_ms[k]) / a.steps, 2) for k in range(3)],
                                 "gpu_launches": int(s1.launches - s0.launches)})))
         return

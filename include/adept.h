@@ -134,6 +134,14 @@ typedef struct {
                                  blocks_per_sm picks its variant (2 or 3 split, 1 or 2 FP64) [0] */
   uint32_t physics;           /* ADEPT_PHYS_* bits [0] */
   double msc_range_factor;    /* f of the multiple-scattering step limit [0.04] */
+  int32_t field_max_iterations; /* charged tracks in the field: 0 = the analytic helix [0];
+                                 N > 0 = the paper's chord propagation (Sec. 2.3): linear
+                                 segments of sagitta <= delta_chord_mm, a crossing refined to
+                                 delta_intersection_mm, at most N segments and refinements per
+                                 step; a track whose step needs more is killed, its energy
+                                 counted in killed_MeV */
+  double delta_chord_mm;      /* [0.25] */
+  double delta_intersection_mm; /* [0.001] */
 } adept_options;
 
 /* adept_options.flags: time every generation (its three transport kernels, from the fork to
@@ -277,6 +285,13 @@ int adept_probe_sample(adept_ctx* ctx, int32_t which, int32_t m, int32_t prec, d
  *    loss it fluctuates about: 2 doubles per draw. */
 int adept_probe_continuous(adept_ctx* ctx, int32_t which, int32_t species, int32_t m, int32_t prec,
                            double T, double s, uint32_t event, size_t n, double* host_out);
+/*  - chord: one chord-propagated step (options field_max_iterations > 0) for n points: in
+ *    pos[3n], dir[3n], vol[n], T[n], charge[n] (+-1), s_phys[n]; out 9 doubles per point:
+ *    status (0 reached s_phys, 1 crossed, 2 iteration cap), path length, next volume,
+ *    position (3), direction (3). */
+int adept_probe_chord(adept_ctx* ctx, int32_t prec, const double* host_pos, const double* host_dir,
+                      const int32_t* host_vol, const double* host_T, const int32_t* host_charge,
+                      const double* host_s_phys, size_t n, double* host_out);
 
 /* Table build without any allocation, for callers that cannot allocate device memory:
  * code that runs under a host framework which owns every device allocation (a fixed

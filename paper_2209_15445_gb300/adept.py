@@ -60,7 +60,9 @@ class adept_options(C.Structure):
                 ("max_generation_log", C.c_uint32), ("track_capacity", C.c_uint64),
                 ("tracks_per_MeV", C.c_double), ("flags", C.c_int32),
                 ("blocks_per_sm_species", C.c_int32 * 3), ("fused", C.c_int32),
-                ("physics", C.c_uint32), ("msc_range_factor", C.c_double)]
+                ("physics", C.c_uint32), ("msc_range_factor", C.c_double),
+                ("field_max_iterations", C.c_int32), ("delta_chord_mm", C.c_double),
+                ("delta_intersection_mm", C.c_double)]
 
 
 TRACK_DTYPE = np.dtype([("pdg", "<i4"), ("pad0", "<i4"), ("E", "<f8"), ("pos", "<f8", 3), ("dir", "<f8", 3),
@@ -125,6 +127,7 @@ def load(path: str = LIB_PATH):
             "adept_probe_distance": [vp, i32, dp, dp, i32p, dp, i32p, sz, dp, i32p],
             "adept_probe_sample": [vp, i32, i32, i32, C.c_double, u32, sz, dp],
             "adept_probe_continuous": [vp, i32, i32, i32, i32, C.c_double, C.c_double, u32, sz, dp],
+            "adept_probe_chord": [vp, i32, dp, dp, C.POINTER(C.c_int32), dp, C.POINTER(C.c_int32), dp, sz, dp],
             "adept_build_tables_noalloc": [C.POINTER(adept_material), i32, C.c_double, vp, vp, vp],
         }
         for name, args in sig.items():
@@ -276,6 +279,19 @@ def adept_build_tables_noalloc(materials, range_cut_mm, dev_tables_ptr, dev_cuts
 def adept_probe_sample(h, which, m, prec, E, event, n):
     out = np.zeros((n, 12))
     rc = load().adept_probe_sample(h, which, m, prec, E, event, n, _dp(out))
+    return rc, out
+
+
+def adept_probe_chord(h, prec, pos, d, vol, T, q, s_phys):
+    """one chord-propagated step per point: (n, 9) status, path, next, position, direction"""
+    pos = np.ascontiguousarray(pos, np.float64); d = np.ascontiguousarray(d, np.float64)
+    vol = np.ascontiguousarray(vol, np.int32); T = np.ascontiguousarray(T, np.float64)
+    q = np.ascontiguousarray(q, np.int32); s_phys = np.ascontiguousarray(s_phys, np.float64)
+    n = len(vol)
+    out = np.zeros((n, 9))
+    i32p = C.POINTER(C.c_int32)
+    rc = load().adept_probe_chord(h, prec, _dp(pos), _dp(d), vol.ctypes.data_as(i32p), _dp(T),
+                                  q.ctypes.data_as(i32p), _dp(s_phys), n, _dp(out))
     return rc, out
 
 

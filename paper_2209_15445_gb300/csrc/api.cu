@@ -268,6 +268,12 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (o.physics & ~(ADEPT_PHYS_MSC | ADEPT_PHYS_FLUCT)) return ADEPT_EINVAL;
   if (o.msc_range_factor < 0.0 || !(o.msc_range_factor < 1e30)) return ADEPT_EINVAL;
   if (o.msc_range_factor == 0.0) o.msc_range_factor = 0.04;
+  if (o.field_max_iterations < 0) return ADEPT_EINVAL;
+  if (o.field_max_iterations > 0 && o.fused) return ADEPT_EINVAL;  // the fused kernel has no chord variant
+  if (o.delta_chord_mm < 0.0 || o.delta_intersection_mm < 0.0) return ADEPT_EINVAL;
+  if (o.delta_chord_mm == 0.0) o.delta_chord_mm = 0.25;
+  if (o.delta_intersection_mm == 0.0) o.delta_intersection_mm = 0.001;
+  if (!(o.delta_chord_mm < 1e6 && o.delta_intersection_mm < 1e6)) return ADEPT_EINVAL;
   if (o.block_size == 0) o.block_size = 256;
   if (o.block_size < 32 || o.block_size > 256 || (o.block_size & 31)) return ADEPT_EINVAL;
   if (o.graph_generations < -1 || o.graph_generations > 1024) return ADEPT_EINVAL;
@@ -350,6 +356,9 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   P.steplen = (o.flags & ADEPT_FLAG_STEP_HISTOGRAM) ? steplen : nullptr;
   P.physics = o.physics;
   P.msc_f = o.msc_range_factor;
+  P.chord_iter = o.field_max_iterations;
+  P.delta_chord = o.delta_chord_mm;
+  P.delta_int = o.delta_intersection_mm;
   c->steplen = steplen;
   // device state
   adept_ctx* c_ = cp;
@@ -387,7 +396,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
       int mb = o.blocks_per_sm_species[sp] > 0 ? o.blocks_per_sm_species[sp] : o.blocks_per_sm;
       if (mb <= 0) mb = o.precision ? 3 : 2;
       c->minb[sp] = std::min(4, mb);
-      int bps = transport_max_blocks_per_sm(o.precision, sp, c->minb[sp], o.block_size);
+      int bps = transport_max_blocks_per_sm(o.precision, sp, c->minb[sp], o.block_size, o.field_max_iterations > 0);
       c->grid[sp] = sms * (bps < 1 ? 1 : bps);
     }
     if (o.fused) {
@@ -1029,6 +1038,37 @@ extern "C" int adept_probe_sample(adept_ctx* c, int32_t which, int32_t m, int32_
   double* dout = reinterpret_cast<double*>(c->probe);
   CK(launch_probe_sample(c->P, which, m, prec, E, event, (int)n, dout, c->stream));
   CK(cudaMemcpyAsync(host_out, dout, 96 * n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ADEPT_OK;
+}
+
+extern "C" int adept_probe_chord(adept_ctx* c, int32_t prec, const double* pos, const double* dir, const int32_t* vol,
+                                 const double* T, const int32_t* q, const double* s_phys, size_t n, double* out) {
+  if (!c || (prec != 0 && prec != 1) || (n && (!pos || !dir || !vol || !T || !q || !s_phys || !out)))
+    return ADEPT_EINVAL;
+  if (c->P.chord_iter <= 0) return fail(c, ADEPT_ESTATE, "the context uses the analytic helix (field_max_iterations = 0)");
+  for (size_t i = 0; i < n; ++i)
+    if (vol[i] < 0 || vol[i] >= c->n_vol || (q[i] != 1 && q[i] != -1) || !(T[i] > 0.0) || !(s_phys[i] >= 0.0))
+      return fail(c, ADEPT_EINVAL, "point %zu: bad volume, charge, energy or step", i);
+  // in: pos 24, dir 24, vol 4, T 8, q 4, s 8 bytes; out 72 bytes
+  const size_t per = 24 + 24 + 8 + 8 + 8 + 8 + 72;
+  if (n > c->probe_bytes / per) return fail(c, ADEPT_EINVAL, "at most %zu points per call", c->probe_bytes / per);
+  char* b = c->probe;
+  double* dpos = reinterpret_cast<double*>(b); b += 24 * n;
+  double* ddir = reinterpret_cast<double*>(b); b += 24 * n;
+  double* dT = reinterpret_cast<double*>(b); b += 8 * n;
+  double* ds = reinterpret_cast<double*>(b); b += 8 * n;
+  double* dout = reinterpret_cast<double*>(b); b += 72 * n;
+  int* dvol = reinterpret_cast<int*>(b); b += 8 * n;
+  int* dq = reinterpret_cast<int*>(b);
+  CK(cudaMemcpyAsync(dpos, pos, 24 * n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(ddir, dir, 24 * n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(dT, T, 8 * n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(ds, s_phys, 8 * n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(dvol, vol, 4 * n, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(dq, q, 4 * n, cudaMemcpyHostToDevice, c->stream));
+  CK(launch_probe_chord(c->P, prec, dpos, ddir, dvol, dT, dq, ds, (int)n, dout, c->stream));
+  CK(cudaMemcpyAsync(out, dout, 72 * n, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return ADEPT_OK;
 }

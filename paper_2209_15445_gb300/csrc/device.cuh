@@ -814,6 +814,123 @@ __device__ __forceinline__ void helix_move(double B, double T, int q, R s, doubl
   u[0] = u0; u[1] = u1;
 }
 
+// ---------------------------------------------------------------- chord propagation (optional)
+// is (x, y, z) inside (or on the boundary of) volume vol
+__device__ __forceinline__ bool inside_volume(const GeoView& g, double x, double y, double z, int vol) {
+  if (g.kind == 0)
+    return z >= __ldg(g.bnd + vol) && z <= __ldg(g.bnd + vol + 1) && fabs(x) <= g.half_xy && fabs(y) <= g.half_xy;
+  const double r2 = x * x + y * y;
+  if (fabs(z) > g.half_z) return false;
+  const double Ro = __ldg(g.bnd + vol);
+  if (r2 > Ro * Ro) return false;
+  if (vol == 0) return true;
+  const double Ri = __ldg(g.bnd + vol - 1);
+  return r2 >= Ri * Ri;
+}
+
+// Chord propagation in the field (paper Sec. 2.3): the helix is followed in linear segments
+// whose sagitta kappa l^2 / 8 is at most dchord (kappa = |du/ds| = u_T kpath); a segment that
+// meets the boundary of the volume (straight distance along it) is refined by bisection
+// between an inside and an outside point of the curve until the sagitta is at most dint,
+// and the crossing is taken on that last chord. Every segment and every bisection is one
+// iteration. Returns 0 (reached s_phys), 1 (crossed into *next) or 2 (more than max_iter
+// iterations: the step did not finish; nothing moved). Curve points are evaluated from the
+// step's start. Not inlined: it runs only when the chord propagator is chosen, and keeps
+// its registers out of the transport kernels.
+template <class R>
+__device__ __forceinline__ int chord_step(const GeoView& g, double B, double T, int q, R s_phys, int max_iter, R dchord,
+                                       R dint, double* x, double* y, double* z, R* u, int vol, int* next, R* s_done) {
+  Helix<R> H;
+  helix_setup<R>(B, T, q, u, *x, *y, H);
+  if (H.straight) {  // no curvature: one straight segment
+    int nx;
+    const R sg = straight_distance<R>(g, *x, *y, *z, u, vol, &nx);
+    const R s = sg <= s_phys ? sg : s_phys;
+    *x += to_d<R>(s * u[0]); *y += to_d<R>(s * u[1]); *z += to_d<R>(s * u[2]);
+    *next = nx;
+    *s_done = s;
+    return sg <= s_phys ? 1 : 0;
+  }
+  const double xs = *x, ys = *y, zs = *z;
+  const R us0 = u[0], us1 = u[1], us2 = u[2];
+  auto at = [&](R s, double& px, double& py, double& pz, R* pu) {
+    px = xs; py = ys; pz = zs;
+    pu[0] = us0; pu[1] = us1; pu[2] = us2;
+    helix_move<R>(B, T, q, s, &px, &py, &pz, pu);
+  };
+  const R kappa = H.uT * H.kpath;
+  const R lmax = M<R>::sqrt((R)8 * dchord / kappa), lint = M<R>::sqrt((R)8 * dint / kappa);
+  R s0 = 0;
+  double p0x = xs, p0y = ys, p0z = zs;
+  R tmp[3];
+  int iters = 0;
+  for (;;) {
+    if (++iters > max_iter) return 2;
+    const R ell = (s_phys - s0 < lmax) ? s_phys - s0 : lmax;
+    double p1x, p1y, p1z;
+    R u1[3];
+    at(s0 + ell, p1x, p1y, p1z, u1);
+    const double dx = p1x - p0x, dy = p1y - p0y, dz = p1z - p0z;
+    const double L = sqrt(dx * dx + dy * dy + dz * dz);
+    int nx = vol;
+    R sb = M<R>::big();
+    if (L > 0.0) {
+      const R d[3] = {to_r<R>(dx / L), to_r<R>(dy / L), to_r<R>(dz / L)};
+      sb = straight_distance<R>(g, p0x, p0y, p0z, d, vol, &nx);
+    }
+    R hi = (R)-1;
+    if (sb < to_r<R>(L)) {  // the segment meets the boundary: a curve point outside?
+      if (!inside_volume(g, p1x, p1y, p1z, vol)) {
+        hi = s0 + ell;
+      } else {
+        const R sc = s0 + ell * (sb / to_r<R>(L));
+        double pcx, pcy, pcz;
+        at(sc, pcx, pcy, pcz, tmp);
+        if (!inside_volume(g, pcx, pcy, pcz, vol)) hi = sc;
+      }
+    }
+    if (hi < (R)0) {  // no crossing on this segment
+      s0 += ell;
+      p0x = p1x; p0y = p1y; p0z = p1z;
+      if (s0 >= s_phys) {
+        *x = p1x; *y = p1y; *z = p1z;
+        u[0] = u1[0]; u[1] = u1[1]; u[2] = u1[2];
+        *s_done = s_phys;
+        return 0;
+      }
+      continue;
+    }
+    R lo = s0;
+    double plx = p0x, ply = p0y, plz = p0z, phx, phy, phz;
+    at(hi, phx, phy, phz, tmp);
+    while (hi - lo > lint) {
+      if (++iters > max_iter) return 2;
+      const R mid = (R)0.5 * (lo + hi);
+      double pmx, pmy, pmz;
+      at(mid, pmx, pmy, pmz, tmp);
+      if (inside_volume(g, pmx, pmy, pmz, vol)) { lo = mid; plx = pmx; ply = pmy; plz = pmz; }
+      else { hi = mid; phx = pmx; phy = pmy; phz = pmz; }
+    }
+    const double ex = phx - plx, ey = phy - ply, ez = phz - plz;
+    const double Le = sqrt(ex * ex + ey * ey + ez * ez);
+    R sx = hi;
+    if (Le > 0.0) {
+      const R e[3] = {to_r<R>(ex / Le), to_r<R>(ey / Le), to_r<R>(ez / Le)};
+      R sbe = straight_distance<R>(g, plx, ply, plz, e, vol, &nx);
+      if (sbe > to_r<R>(Le)) sbe = to_r<R>(Le);
+      sx = lo + (sbe / to_r<R>(Le)) * (hi - lo);
+      *x = plx + to_d<R>(sbe) * (ex / Le); *y = ply + to_d<R>(sbe) * (ey / Le); *z = plz + to_d<R>(sbe) * (ez / Le);
+    } else {
+      *x = phx; *y = phy; *z = phz;
+    }
+    double qx, qy, qz;
+    at(sx, qx, qy, qz, u);
+    *next = nx;
+    *s_done = sx;
+    return 1;
+  }
+}
+
 // locate a point: on a surface, the volume the direction points into
 __device__ __forceinline__ int locate(const GeoView& g, double x, double y, double z, double ux, double uy,
                                       double uz) {

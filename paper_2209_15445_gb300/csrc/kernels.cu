@@ -196,41 +196,6 @@ cudaError_t launch_build_tables(const Params& P, const double* mat_in, int n_mat
   return cudaGetLastError();
 }
 
-// One generation of one species (paper Sec. 3: TransportElectrons, TransportPositrons and
-// TransportGammas). Persistent launch: each warp takes 32-track tiles of the current queue.
-// The three species kernels of a generation are independent (each reads its own current
-// queue and appends to the next ones atomically), so they run concurrently on three
-// streams; k_close_generation then publishes the next queue sizes.
-template <class R, int S, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
-  __shared__ unsigned long long s_steps, s_created[3];
-  __shared__ WarpRing<R> rings[8];
-  const uint32_t gen = __ldcg(&P.ctrl->gen);
-  const int p = gen & 1;
-  if (threadIdx.x == 0) { s_steps = 0; s_created[0] = s_created[1] = s_created[2] = 0; }
-  __syncthreads();
-  // injection may have counted past the capacity (those tracks were dropped)
-  const uint32_t n = min(__ldcg(&P.ctrl->count[p][S]), P.cap);
-  const uint32_t tiles = (n + 31) >> 5;
-  const uint32_t wpb = blockDim.x >> 5;
-  WarpRing<R>& ring = rings[threadIdx.x >> 5];
-  uint32_t head = 0, tail = 0;
-  unsigned long long nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
-  for (uint32_t tile = blockIdx.x * wpb + (threadIdx.x >> 5); tile < tiles; tile += gridDim.x * wpb)
-    run_tile<R, S>(P, p, tile << 5, n, ring, head, tail, nsteps, ncreated);
-  if (tail != head) drain<R, S>(P, p, ring, head, tail - head, ncreated);
-  if ((threadIdx.x & 31) == 0) {
-    if (nsteps[S]) atomicAdd(&s_steps, nsteps[S]);
-    for (int k = 0; k < 3; ++k)
-      if (ncreated[k]) atomicAdd(&s_created[k], ncreated[k]);
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  if (s_steps) atomicAdd(&P.ctrl->steps[S], s_steps);
-  for (int k = 0; k < 3; ++k)
-    if (s_created[k]) atomicAdd(&P.ctrl->created[k], s_created[k]);
-}
-
 // The three species kernels of a generation run concurrently; this closes it after them.
 __global__ void k_close_generation(Params P) {
   if (threadIdx.x == 0) close_generation(P);
@@ -258,18 +223,24 @@ static const void* transport_fn(int species, int minb) {
   return species == 0 ? transport_fn<R, 0>(minb) : (species == 1 ? transport_fn<R, 1>(minb) : transport_fn<R, 2>(minb));
 }
 
-int transport_max_blocks_per_sm(int precision, int species, int minb, int block) {
+// the kernel of species `species` for these options: the chord-propagator variant for
+// charged species when P.chord_iter > 0
+static const void* pick_transport(int precision, int species, int minb, bool chord) {
+  if (chord && species != 0) return chord_transport_fn(precision, species, minb);
+  return precision ? transport_fn<float>(species, minb) : transport_fn<double>(species, minb);
+}
+
+int transport_max_blocks_per_sm(int precision, int species, int minb, int block, bool chord) {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &n, precision ? transport_fn<float>(species, minb) : transport_fn<double>(species, minb), block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick_transport(precision, species, minb, chord), block, 0);
   return n;
 }
 
 cudaError_t launch_transport(const Params& P, int precision, int species, int minb, int grid, int block,
                              cudaStream_t st) {
   void* args[] = {const_cast<Params*>(&P)};
-  return cudaLaunchKernel(precision ? transport_fn<float>(species, minb) : transport_fn<double>(species, minb),
-                          dim3(grid), dim3(block), args, 0, st);
+  return cudaLaunchKernel(pick_transport(precision, species, minb, P.chord_iter > 0), dim3(grid), dim3(block), args,
+                          0, st);
 }
 
 // ======================================================================== admission
@@ -430,6 +401,32 @@ cudaError_t launch_probe_distance(const Params& P, int prec, const double* pos, 
   if (n <= 0) return cudaSuccess;
   if (prec) k_probe_distance<float><<<(n + 127) / 128, 128, 0, st>>>(P, pos, dir, vol, T, q, n, s, next);
   else k_probe_distance<double><<<(n + 127) / 128, 128, 0, st>>>(P, pos, dir, vol, T, q, n, s, next);
+  return cudaGetLastError();
+}
+
+// out per point: status, path, next, x, y, z, ux, uy, uz, iterations unused (9 doubles used)
+template <class R>
+__global__ void k_probe_chord(Params P, const double* pos, const double* dir, const int* vol, const double* T,
+                              const int* q, const double* s_phys, int n, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  R u[3] = {(R)dir[3 * i], (R)dir[3 * i + 1], (R)dir[3 * i + 2]};
+  double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  int nx = vol[i];
+  R sd = 0;
+  const int rc = chord_step<R>(P.geo, P.field_T, T[i], q[i], (R)s_phys[i], P.chord_iter, (R)P.delta_chord,
+                               (R)P.delta_int, &x, &y, &z, u, vol[i], &nx, &sd);
+  double* o = out + 9 * (size_t)i;
+  o[0] = rc; o[1] = sd; o[2] = nx;
+  o[3] = x; o[4] = y; o[5] = z;
+  o[6] = u[0]; o[7] = u[1]; o[8] = u[2];
+}
+
+cudaError_t launch_probe_chord(const Params& P, int prec, const double* pos, const double* dir, const int* vol,
+                               const double* T, const int* q, const double* s_phys, int n, double* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (prec) k_probe_chord<float><<<(n + 127) / 128, 128, 0, st>>>(P, pos, dir, vol, T, q, s_phys, n, out);
+  else k_probe_chord<double><<<(n + 127) / 128, 128, 0, st>>>(P, pos, dir, vol, T, q, s_phys, n, out);
   return cudaGetLastError();
 }
 

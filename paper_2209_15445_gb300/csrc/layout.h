@@ -110,6 +110,9 @@ struct Params {
   unsigned long long* steplen;  // [3][64] step-length histogram (log2 bins), or null
   uint32_t physics;     // ADEPT_PHYS_* bits: multiple scattering, loss fluctuations
   double msc_f;         // multiple-scattering step limit: s <= max(msc_f R, 0.01 mm)
+  int chord_iter;       // 0: analytic helix; N > 0: chord propagation capped at N iterations
+  double delta_chord;   // chord sagitta limit, mm
+  double delta_int;     // intersection accuracy, mm
 };
 
 // device view of one submitted particle; same layout as adept_track in adept.h
@@ -153,7 +156,11 @@ cudaError_t launch_probe_distance(const Params& P, int prec, const double* pos, 
                                   int* next, cudaStream_t st);
 cudaError_t launch_probe_sample(const Params& P, int which, int m, int prec, double E, uint32_t event,
                                 int n, double* out, cudaStream_t st);
-int transport_max_blocks_per_sm(int precision, int species, int minb, int block);
+int transport_max_blocks_per_sm(int precision, int species, int minb, int block, bool chord);
+// the chord-propagator variant of the e- (species 1) or e+ (2) kernel, 2 or 3 blocks/SM
+const void* chord_transport_fn(int precision, int species, int minb);
+cudaError_t launch_probe_chord(const Params& P, int prec, const double* pos, const double* dir, const int* vol,
+                               const double* T, const int* q, const double* s_phys, int n, double* out, cudaStream_t st);
 cudaError_t launch_probe_continuous(const Params& P, int which, int species, int m, int prec, double T, double s,
                                     uint32_t event, int n, double* out, cudaStream_t st);
 // one kernel per generation for all species; its last block closes the generation

@@ -97,8 +97,10 @@ enum Outcome { kDead = 0, kAlive = 1, kInteract = 2 };
 // distance (S5/S6), move, continuous loss (S7) and boundary crossing (S8). A step that
 // ends in a discrete interaction returns kInteract with the chosen process; the
 // interaction itself (S9) runs later on a full warp. dep is the energy to score in
-// dep_bin; sec receives the two photons of a positron that stops.
-template <class R, int S>
+// dep_bin; sec receives the two photons of a positron that stops. CH compiles in the
+// chord propagator of the field (used when P.chord_iter > 0), kept out of the kernels
+// that run the analytic helix.
+template <class R, int S, bool CH = false>
 __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>& sec, double& dep, int& dep_bin,
                                               uint32_t& pstep, int& proc) {
   constexpr int q = S == 1 ? -1 : (S == 2 ? 1 : 0);
@@ -172,16 +174,29 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
   // S5/S6: distance to the boundary along the straight line or helix
   int next;
   const bool field = (q != 0) && (P.field_T != 0.0);
-  const R s_geom = field ? helix_distance<R>(P.geo, P.field_T, t.E, q, t.x, t.y, t.z, t.u, vol, &next)
-                         : straight_distance<R>(P.geo, t.x, t.y, t.z, t.u, vol, &next);
-  const bool boundary = s_geom <= s_phys;
-  const R s = boundary ? s_geom : s_phys;
-  if (field) {
-    helix_move<R>(P.field_T, t.E, q, s, &t.x, &t.y, &t.z, t.u);
+  bool boundary;
+  R s;
+  if constexpr (CH) {
+    // chord propagation (paper Sec. 2.3): a step whose integration does not finish within
+    // the iteration cap kills its track, with the energy accounted
+    R sd;
+    const int rc = chord_step<R>(P.geo, P.field_T, t.E, q, s_phys, P.chord_iter, (R)P.delta_chord, (R)P.delta_int,
+                                 &t.x, &t.y, &t.z, t.u, vol, &next, &sd);
+    if (rc == 2) { atomicAdd(P.evt.killed + t.ev, t.E + rest); return kDead; }
+    boundary = rc == 1;
+    s = sd;
   } else {
-    t.x += to_d<R>(s * t.u[0]);
-    t.y += to_d<R>(s * t.u[1]);
-    t.z += to_d<R>(s * t.u[2]);
+    const R s_geom = field ? helix_distance<R>(P.geo, P.field_T, t.E, q, t.x, t.y, t.z, t.u, vol, &next)
+                           : straight_distance<R>(P.geo, t.x, t.y, t.z, t.u, vol, &next);
+    boundary = s_geom <= s_phys;
+    s = boundary ? s_geom : s_phys;
+    if (field) {
+      helix_move<R>(P.field_T, t.E, q, s, &t.x, &t.y, &t.z, t.u);
+    } else {
+      t.x += to_d<R>(s * t.u[0]);
+      t.y += to_d<R>(s * t.u[1]);
+      t.z += to_d<R>(s * t.u[2]);
+    }
   }
   if (boundary && P.geo.kind == 0 && next >= 0) t.z = __ldg(P.geo.bnd + (t.u[2] > (R)0 ? vol + 1 : vol));
   t.step = step + 1;
@@ -364,7 +379,7 @@ __device__ __forceinline__ void drain(const Params& P, int p, WarpRing<R>& ring,
 
 // One warp takes 32 consecutive tracks of species S: phase A for each, appends the
 // survivors, queues the interactions and runs full warps of them as they accumulate.
-template <class R, int S>
+template <class R, int S, bool CH = false>
 __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, uint32_t n, WarpRing<R>& ring,
                                          uint32_t& head, uint32_t& tail, unsigned long long* nsteps,
                                          unsigned long long* ncreated) {
@@ -381,7 +396,7 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
     load_track<R>(P.qd[3 * p + S], i, t);
     double dep = 0.0;
     int dep_bin = -1;
-    outcome = step_transport<R, S>(P, t, sec, dep, dep_bin, pstep, proc);
+    outcome = step_transport<R, S, CH>(P, t, sec, dep, dep_bin, pstep, proc);
     // S10: score the step's deposit in (event, layer, material)
     score(P, t.ev, dep_bin, dep);
   }
@@ -401,6 +416,42 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
     head += 32u;
     __syncwarp();
   }
+}
+
+// One generation of one species (paper Sec. 3: TransportElectrons, TransportPositrons and
+// TransportGammas). Persistent launch: each warp takes 32-track tiles of the current queue.
+// The three species kernels of a generation are independent (each reads its own current
+// queue and appends to the next ones atomically), so they run concurrently on three
+// streams; k_close_generation then publishes the next queue sizes.
+// CH: the chord-propagator variant (chord.cu instantiates it for e- and e+).
+template <class R, int S, int MINB, bool CH = false>
+__global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
+  __shared__ unsigned long long s_steps, s_created[3];
+  __shared__ WarpRing<R> rings[8];
+  const uint32_t gen = __ldcg(&P.ctrl->gen);
+  const int p = gen & 1;
+  if (threadIdx.x == 0) { s_steps = 0; s_created[0] = s_created[1] = s_created[2] = 0; }
+  __syncthreads();
+  // injection may have counted past the capacity (those tracks were dropped)
+  const uint32_t n = min(__ldcg(&P.ctrl->count[p][S]), P.cap);
+  const uint32_t tiles = (n + 31) >> 5;
+  const uint32_t wpb = blockDim.x >> 5;
+  WarpRing<R>& ring = rings[threadIdx.x >> 5];
+  uint32_t head = 0, tail = 0;
+  unsigned long long nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
+  for (uint32_t tile = blockIdx.x * wpb + (threadIdx.x >> 5); tile < tiles; tile += gridDim.x * wpb)
+    run_tile<R, S, CH>(P, p, tile << 5, n, ring, head, tail, nsteps, ncreated);
+  if (tail != head) drain<R, S>(P, p, ring, head, tail - head, ncreated);
+  if ((threadIdx.x & 31) == 0) {
+    if (nsteps[S]) atomicAdd(&s_steps, nsteps[S]);
+    for (int k = 0; k < 3; ++k)
+      if (ncreated[k]) atomicAdd(&s_created[k], ncreated[k]);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (s_steps) atomicAdd(&P.ctrl->steps[S], s_steps);
+  for (int k = 0; k < 3; ++k)
+    if (s_created[k]) atomicAdd(&P.ctrl->created[k], s_created[k]);
 }
 
 // Close a generation once the species kernels are done: publish the next queue sizes
