@@ -56,7 +56,8 @@ class _Result(C.Structure):
     _fields_ = [("edep", C.POINTER(C.c_double)), ("leaked", C.POINTER(C.c_double)),
                 ("killed", C.POINTER(C.c_double)), ("steps", C.c_uint64 * 3),
                 ("created", C.c_uint64 * 3), ("gen_hist", C.POINTER(C.c_uint64)),
-                ("steplen_hist", C.POINTER(C.c_uint64))]
+                ("steplen_hist", C.POINTER(C.c_uint64)), ("leak_out", C.POINTER(C.c_double)),
+                ("leak_cap", C.c_uint64), ("leak_n", C.c_uint64)]
 
 
 def lib():
@@ -238,7 +239,8 @@ class Oracle:
 
     def transport(self, prim, seed=1, process_mask=0, max_steps=100000, max_vacuum_steps=1000,
                   n_threads=None, max_gen=0, steplen=False, event_slot=None, n_events=None,
-                  physics=0, msc_range_factor=0.0, field_max_iter=0, delta_chord=0.0, delta_int=0.0):
+                  physics=0, msc_range_factor=0.0, field_max_iter=0, delta_chord=0.0, delta_int=0.0,
+                  outgoing=0):
         """Transport primaries; tracks with the same event number form one event (slot
         order = first appearance) unless event_slot is given."""
         n = len(prim)
@@ -259,6 +261,9 @@ class Oracle:
         res.edep = _dp(edep); res.leaked = _dp(leaked); res.killed = _dp(killed)
         res.gen_hist = gen.ctypes.data_as(C.POINTER(C.c_uint64)) if max_gen > 0 else None
         res.steplen_hist = sl.ctypes.data_as(C.POINTER(C.c_uint64)) if steplen else None
+        leak = np.zeros((max(outgoing, 1), 9))
+        res.leak_out = _dp(leak) if outgoing else None
+        res.leak_cap = outgoing
         o = _RunOpts(seed, process_mask, max_steps, max_vacuum_steps,
                      n_threads or os.cpu_count() or 1, max_gen, physics, msc_range_factor, field_max_iter,
                      delta_chord, delta_int)
@@ -278,6 +283,10 @@ class Oracle:
             out["gen_hist"] = gen
         if steplen:
             out["steplen"] = sl
+        if outgoing:
+            if res.leak_n > outgoing:
+                raise ValueError(f"{res.leak_n} outgoing particles, room for {outgoing}")
+            out["outgoing"] = leak[: res.leak_n]
         return out
 
 

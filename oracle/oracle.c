@@ -1287,7 +1287,22 @@ typedef struct {
   uint64_t steps[3], created[3];
   uint64_t* gen_hist; /* shared, atomically updated */
   uint64_t* steplen;  /* shared */
+  or_result* res;     /* outgoing-particle list (shared, atomically indexed) */
+  int slot;
 } ev_t;
+
+/* an outgoing particle: the track as it leaves the calorimeter */
+static void record_leak(ev_t* e, const trk_t* t) {
+  or_result* r = e->res;
+  if (!r->leak_out) return;
+  const uint64_t i = __atomic_fetch_add(&r->leak_n, 1, __ATOMIC_RELAXED);
+  if (i >= r->leak_cap) return;
+  double* o = r->leak_out + 9 * i;
+  o[0] = e->slot;
+  o[1] = t->species == 0 ? 22 : (t->species == 1 ? 11 : -11);
+  o[2] = t->T;
+  for (int a = 0; a < 3; ++a) { o[3 + a] = t->x[a]; o[6 + a] = t->u[a]; }
+}
 
 static int enabled(const or_run_opts* o, uint32_t bit) {
   return o->process_mask == 0 || (o->process_mask & bit);
@@ -1473,7 +1488,7 @@ static int step_track(ev_t* e, trk_t* t, stack_t_* st) {
   }
 
   if (boundary) {
-    if (next < 0) { e->leaked += t->T + rest; return 0; }
+    if (next < 0) { e->leaked += t->T + rest; record_leak(e, t); return 0; }
     t->vol = next;
     return 1;
   }
@@ -1533,6 +1548,8 @@ static void run_event(job_t* j, int ev, stack_t_* st) {
   e.edep = j->r->edep + (size_t)ev * c->n_bins;
   e.gen_hist = j->r->gen_hist;
   e.steplen = j->r->steplen_hist;
+  e.res = j->r;
+  e.slot = ev; /* tracks are grouped by event slot */
   st->n = 0;
   for (int k = j->ev_begin[ev + 1] - 1; k >= j->ev_begin[ev]; --k) {
     const int i = j->order[k];
@@ -1544,7 +1561,7 @@ static void run_event(job_t* j, int ev, stack_t_* st) {
     t.id = (uint64_t)(k - j->ev_begin[ev] + 1);
     e.event = j->key[i];
     t.vol = or_locate(c, t.x, t.u);
-    if (t.vol < 0) { e.leaked += t.T + (t.species == 2 ? 2.0 * kMe : 0.0); continue; }
+    if (t.vol < 0) { e.leaked += t.T + (t.species == 2 ? 2.0 * kMe : 0.0); record_leak(&e, &t); continue; }
     push(st, &t);
   }
   while (st->n > 0) {

@@ -158,6 +158,12 @@ typedef struct {
   uint64_t created[3]; /* secondaries pushed per species */
   uint64_t* gen_hist;  /* [max_gen][3] steps per generation and species, or NULL */
   uint64_t* steplen_hist; /* [3][64] log2 bins of step length in um, or NULL */
+  /* outgoing particles (tracks that leave the calorimeter, primaries submitted outside it):
+   * 9 doubles each (event slot, pdg, kinetic energy, position[3], direction[3]) at the point
+   * where they leave; up to leak_cap records, leak_n counts all (NULL: not recorded) */
+  double* leak_out;
+  uint64_t leak_cap;
+  uint64_t leak_n;
 } or_result;
 
 /* tracks: pdg (22, 11, -11), kinetic energy, position, direction, RNG event key, event slot */
