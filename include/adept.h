@@ -142,6 +142,9 @@ typedef struct {
                                  counted in killed_MeV */
   double delta_chord_mm;      /* [0.25] */
   double delta_intersection_mm; /* [0.001] */
+  uint32_t max_outgoing;      /* outgoing particles kept between two status reads (a ring in the
+                                 arena, 64 bytes each); more make adept_transport return
+                                 ADEPT_ENOMEM [1048576] */
 } adept_options;
 
 /* adept_options.flags: time every generation (its three transport kernels, from the fork to
@@ -174,6 +177,13 @@ typedef struct {
   double killed_MeV;   /* energy of tracks stopped by the step caps or by overflow */
   double latency_us;   /* from adept_submit to completion being seen by the host */
 } adept_result;
+
+/* Outgoing particles of a finished request (paper Sec. 4: the particles that leave the GPU
+ * region go back to the host): every track that left the calorimeter, at the point where it
+ * left, and every primary submitted outside it, with the caller's event number. Writes
+ * min(n_max, count) of them to out (unordered) and the count to *n_out. Call it before
+ * adept_get_scoring, which releases the request. ADEPT_EBUSY before the request is done. */
+int adept_get_leaked(adept_ctx* ctx, uint32_t request, adept_track* out, size_t n_max, size_t* n_out);
 
 /* Global counters since adept_init. */
 typedef struct {

@@ -62,7 +62,7 @@ class adept_options(C.Structure):
                 ("blocks_per_sm_species", C.c_int32 * 3), ("fused", C.c_int32),
                 ("physics", C.c_uint32), ("msc_range_factor", C.c_double),
                 ("field_max_iterations", C.c_int32), ("delta_chord_mm", C.c_double),
-                ("delta_intersection_mm", C.c_double)]
+                ("delta_intersection_mm", C.c_double), ("max_outgoing", C.c_uint32)]
 
 
 TRACK_DTYPE = np.dtype([("pdg", "<i4"), ("pad0", "<i4"), ("E", "<f8"), ("pos", "<f8", 3), ("dir", "<f8", 3),
@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH):
             "adept_poll": [vp, u32],
             "adept_wait": [vp, u32, u64],
             "adept_get_scoring": [vp, u32, dp, sz, C.POINTER(adept_result)],
+            "adept_get_leaked": [vp, u32, C.c_void_p, sz, C.POINTER(C.c_size_t)],
             "adept_get_stats": [vp, C.POINTER(adept_stats)],
             "adept_get_generation_log": [vp, u32p, sz],
             "adept_reset_generation_log": [vp],
@@ -282,6 +283,18 @@ def adept_probe_sample(h, which, m, prec, E, event, n):
     return rc, out
 
 
+def adept_get_leaked(h, rid):
+    """(rc, structured array of adept_track) of a finished request's outgoing particles"""
+    n = C.c_size_t()
+    L = load()
+    rc = L.adept_get_leaked(h, rid, None, 0, C.byref(n))
+    if rc != OK:
+        return rc, None
+    arr = np.zeros(n.value, dtype=TRACK_DTYPE)
+    rc = L.adept_get_leaked(h, rid, arr.ctypes.data_as(C.c_void_p), n.value, C.byref(n))
+    return rc, arr
+
+
 def adept_probe_chord(h, prec, pos, d, vol, T, q, s_phys):
     """one chord-propagated step per point: (n, 9) status, path, next, position, direction"""
     pos = np.ascontiguousarray(pos, np.float64); d = np.ascontiguousarray(d, np.float64)
@@ -370,6 +383,12 @@ class Transport:
 
     def transport(self, timeout_us=0):
         return self.check(adept_transport(self.h, timeout_us))
+
+    def outgoing(self, rid):
+        """the outgoing particles of a finished request (before result(), which releases it)"""
+        rc, arr = adept_get_leaked(self.h, rid)
+        self.check(rc)
+        return arr
 
     def result(self, rid, n_events):
         out = np.zeros((n_events, self.n_bins))

@@ -46,6 +46,7 @@ struct Request {
   int state = 0;                       // 0 pending, 1 in flight, 2 done
   Clock::time_point t_submit, t_done;
   std::vector<double> edep, leaked, killed;
+  std::vector<adept_track> outgoing;   // particles that left the calorimeter
 };
 
 struct SlotAlloc {  // first-fit allocator of contiguous event-slot ranges
@@ -109,6 +110,9 @@ struct adept_ctx {
   bool built = false;
   // host pinned buffers
   Ctrl* h_ctrl[2] = {nullptr, nullptr};     // status of the two chunks that may be in flight
+  unsigned long long* h_floor[2] = {nullptr, nullptr};  // outgoing-ring read position at each launch
+  unsigned long long leak_read = 0, leak_dropped_seen = 0;  // host read position, drops seen
+  std::vector<LeakRec> leak_tmp;
   uint32_t* h_done[2] = {nullptr, nullptr};
   cudaEvent_t status_ev[2] = {nullptr, nullptr};
   cudaEvent_t stage_ev = nullptr;            // the last copy out of the pinned staging buffer
@@ -285,6 +289,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (o.max_events == 0) o.max_events = 65536;
   if (o.max_generation_log == 0) o.max_generation_log = 4096;
   if (o.max_generation_log > (uint32_t)kMaxLogGen) o.max_generation_log = kMaxLogGen;
+  if (o.max_outgoing == 0) o.max_outgoing = 1u << 20;
   if (!(o.tracks_per_MeV > 0.0)) o.tracks_per_MeV = 0.25;
   c->range_cut = cuts->range_cut_mm;
   int rc = build_geometry(c.get(), geometry);
@@ -314,6 +319,8 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   ok = ok && carve_n(cp, &steplen, 3 * 64);
   TrackSoA* qdesc = nullptr;
   ok = ok && carve_n(cp, &qdesc, 6);
+  ok = ok && carve_n(cp, &P.leak, o.max_outgoing);
+  P.leak_cap = o.max_outgoing;
   c->probe_bytes = (size_t)8 << 20;
   c->probe = static_cast<char*>(carve(cp, c->probe_bytes));
   ok = ok && c->probe;
@@ -373,6 +380,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     CK(cudaMemsetAsync(E.state, 0, sizeof(uint32_t) * ms, c->stream));
     for (int b = 0; b < 2; ++b) {
       CK(cudaHostAlloc(&c->h_ctrl[b], sizeof(Ctrl), cudaHostAllocDefault));
+      CK(cudaHostAlloc(&c->h_floor[b], sizeof(unsigned long long), cudaHostAllocDefault));
       CK(cudaHostAlloc(&c->h_done[b], sizeof(uint32_t) * kDoneChunk, cudaHostAllocDefault));
       CK(cudaEventCreateWithFlags(&c->status_ev[b], cudaEventDisableTiming));
     }
@@ -663,6 +671,10 @@ static int capture_graph(adept_ctx* c, int gens, int b) {
 static int launch_chunk(adept_ctx* c, int b) {
   const int G = c->opt.graph_generations;
   const int gens = G > 0 ? G : 1;
+  // the outgoing ring may be written up to the host's read position plus its capacity
+  *c->h_floor[b] = c->leak_read;
+  CK(cudaMemcpyAsync(&c->P.ctrl->leak_floor, c->h_floor[b], sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                     c->stream));
   if (timing(c)) {
     int rc = ensure_events(c, 8 * gens);
     if (rc) return rc;
@@ -711,6 +723,44 @@ static int wait_chunk(adept_ctx* c, int b) {
     }
     c->stats.step_launches += gens;
   }
+  return ADEPT_OK;
+}
+
+// Outgoing particles recorded up to the end of chunk b: copy them out of the ring and give
+// each to its request. Records the device could not write (ring full) are counted; they
+// make the transport fail with ADEPT_ENOMEM like a queue overflow.
+static int collect_outgoing(adept_ctx* c, const Ctrl& h, int b, int* stop_rc) {
+  const unsigned long long cap = c->P.leak_cap;
+  const unsigned long long end = std::min<unsigned long long>(h.leak_count, *c->h_floor[b] + cap);
+  if (end > c->leak_read) {
+    const size_t n = (size_t)(end - c->leak_read);
+    c->leak_tmp.resize(n);
+    const size_t start = (size_t)(c->leak_read % cap);
+    const size_t first = std::min<size_t>(n, (size_t)cap - start);
+    CK(cudaMemcpyAsync(c->leak_tmp.data(), c->P.leak + start, sizeof(LeakRec) * first, cudaMemcpyDeviceToHost,
+                       c->copy_stream));
+    if (first < n)
+      CK(cudaMemcpyAsync(c->leak_tmp.data() + first, c->P.leak, sizeof(LeakRec) * (n - first), cudaMemcpyDeviceToHost,
+                         c->copy_stream));
+    CK(cudaStreamSynchronize(c->copy_stream));
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (const LeakRec& x : c->leak_tmp) {
+      auto it = c->reqs.find(c->slot_req[x.slot]);
+      if (it == c->reqs.end()) continue;
+      Request* r = it->second.get();
+      adept_track t;
+      t.pdg = x.pdg;
+      t.E_kin_MeV = x.E;
+      for (int k = 0; k < 3; ++k) { t.pos_mm[k] = x.pos[k]; t.dir[k] = x.dir[k]; }
+      t.event = r->keys[x.slot - r->slot_base];
+      r->outgoing.push_back(t);
+    }
+  }
+  c->leak_read = std::max<unsigned long long>(c->leak_read, h.leak_count);
+  if (h.leak_dropped > c->leak_dropped_seen && *stop_rc == ADEPT_OK)
+    *stop_rc = fail(c, ADEPT_ENOMEM, "%llu outgoing particles exceeded the ring of %u (max_outgoing); results are "
+                    "incomplete", h.leak_dropped - c->leak_dropped_seen, c->P.leak_cap);
+  c->leak_dropped_seen = h.leak_dropped;
   return ADEPT_OK;
 }
 
@@ -788,6 +838,8 @@ extern "C" int adept_transport(adept_ctx* c, uint64_t timeout_us) {
     for (int k = 0; k < 3; ++k) { c->stats.steps[k] = h.steps[k]; c->stats.secondaries[k] = h.created[k]; }
     c->stats.generations = h.generations;
     c->stats.overflow = h.overflow;
+    rc = collect_outgoing(c, h, b, &stop_rc);
+    if (rc) return rc;
     const uint32_t nd = h.done_count[b];
     done.assign(c->h_done[b], c->h_done[b] + std::min(nd, kDoneChunk));
     if (nd > kDoneChunk) {  // list b is not rewritten before buffer b is queued again
@@ -874,6 +926,19 @@ extern "C" int adept_get_scoring(adept_ctx* c, uint32_t id, double* edep_out, si
     meta->killed_MeV = k;
     meta->latency_us = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
   }
+  return ADEPT_OK;
+}
+
+extern "C" int adept_get_leaked(adept_ctx* c, uint32_t id, adept_track* out, size_t n_max, size_t* n_out) {
+  if (!c || !n_out || (n_max && !out)) return ADEPT_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  auto it = c->reqs.find(id);
+  if (it == c->reqs.end()) return ADEPT_ENOTFOUND;
+  const Request& r = *it->second;
+  if (r.state != 2) return ADEPT_EBUSY;
+  *n_out = r.outgoing.size();
+  const size_t n = std::min(n_max, r.outgoing.size());
+  if (n) memcpy(out, r.outgoing.data(), sizeof(adept_track) * n);
   return ADEPT_OK;
 }
 
@@ -1108,6 +1173,7 @@ extern "C" void adept_destroy(adept_ctx* c) {
   if (c->tjoin) cudaEventDestroy(c->tjoin);
   for (int b = 0; b < 2; ++b) {
     if (c->h_ctrl[b]) cudaFreeHost(c->h_ctrl[b]);
+    if (c->h_floor[b]) cudaFreeHost(c->h_floor[b]);
     if (c->h_done[b]) cudaFreeHost(c->h_done[b]);
     if (c->status_ev[b]) cudaEventDestroy(c->status_ev[b]);
   }

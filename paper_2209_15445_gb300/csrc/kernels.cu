@@ -274,7 +274,11 @@ __global__ void k_init_primaries(Params P, const TrackIn* recs, const uint32_t* 
   const int sp = r.pdg == 22 ? 0 : (r.pdg == 11 ? 1 : 2);
   const double rest = sp == 2 ? 2.0 * kMe : 0.0;
   const int vol = locate(P.geo, r.pos[0], r.pos[1], r.pos[2], r.dir[0], r.dir[1], r.dir[2]);
-  if (vol < 0) { atomicAdd(P.evt.leaked + slot, r.E + rest); return; }
+  if (vol < 0) {
+    atomicAdd(P.evt.leaked + slot, r.E + rest);
+    record_leak(P, r.pdg, slot, r.E, r.pos[0], r.pos[1], r.pos[2], r.dir[0], r.dir[1], r.dir[2]);
+    return;
+  }
   const int p = __ldcg(&P.ctrl->gen) & 1;
   const uint32_t d = atomicAdd(&P.ctrl->count[p][sp], 1u);
   if (d >= P.cap) {

@@ -80,6 +80,19 @@ struct Ctrl {
   unsigned long long created[3];
   unsigned long long overflow;
   unsigned long long generations;
+  // outgoing particles: records appended (ring index = count mod capacity), records not
+  // written because the host had not read far enough, and the host's read position when the
+  // running chunk was launched (a record may go where the host has read)
+  unsigned long long leak_count, leak_dropped, leak_floor;
+};
+
+// one outgoing particle, as it leaves the calorimeter (64 bytes)
+struct LeakRec {
+  int32_t pdg;
+  uint32_t slot;
+  double E;
+  double pos[3];
+  double dir[3];
 };
 
 struct EventView {
@@ -110,6 +123,8 @@ struct Params {
   unsigned long long* steplen;  // [3][64] step-length histogram (log2 bins), or null
   uint32_t physics;     // ADEPT_PHYS_* bits: multiple scattering, loss fluctuations
   double msc_f;         // multiple-scattering step limit: s <= max(msc_f R, 0.01 mm)
+  LeakRec* leak;        // ring of outgoing particles
+  uint32_t leak_cap;
   int chord_iter;       // 0: analytic helix; N > 0: chord propagation capped at N iterations
   double delta_chord;   // chord sagitta limit, mm
   double delta_int;     // intersection accuracy, mm

@@ -74,6 +74,20 @@ __device__ __forceinline__ void store_track<float>(const TrackSoA& q, uint32_t i
   q.meta[i] = make_uint4((uint32_t)id, (uint32_t)(id >> 32), ev, step);
 }
 
+// an outgoing particle (paper Sec. 4: the GPU region hands back the particles that leave it)
+__device__ __forceinline__ void record_leak(const Params& P, int pdg, uint32_t slot, double E, double x, double y,
+                                            double z, double ux, double uy, double uz) {
+  const unsigned long long i = atomicAdd(&P.ctrl->leak_count, 1ull);
+  if (i - __ldcg(&P.ctrl->leak_floor) >= P.leak_cap) {
+    atomicAdd(&P.ctrl->leak_dropped, 1ull);
+    return;
+  }
+  LeakRec& r = P.leak[i % P.leak_cap];
+  r.pdg = pdg; r.slot = slot; r.E = E;
+  r.pos[0] = x; r.pos[1] = y; r.pos[2] = z;
+  r.dir[0] = ux; r.dir[1] = uy; r.dir[2] = uz;
+}
+
 template <class R> __device__ __forceinline__ const typename Pair2<R>::T* tab_g(const TableView& T);
 template <> __device__ __forceinline__ const double2* tab_g<double>(const TableView& T) { return T.g64; }
 template <> __device__ __forceinline__ const float2* tab_g<float>(const TableView& T) { return T.g32; }
@@ -231,7 +245,11 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
   }
   // S8: boundary crossing
   if (boundary) {
-    if (next < 0) { atomicAdd(P.evt.leaked + t.ev, t.E + rest); return kDead; }
+    if (next < 0) {
+      atomicAdd(P.evt.leaked + t.ev, t.E + rest);
+      record_leak(P, S == 0 ? 22 : (S == 1 ? 11 : -11), t.ev, t.E, t.x, t.y, t.z, t.u[0], t.u[1], t.u[2]);
+      return kDead;
+    }
     t.nav = (uint32_t)next | (vac << 16);
     return kAlive;
   }
