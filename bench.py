@@ -49,7 +49,7 @@ NCU_SRC_HASH = "b09af856d4b60efd"
 
 def kernel_src_hash() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "fused.cu", "transport.cuh", "device.cuh", "layout.h"):
+    for f in ("kernels.cu", "transport.cuh", "device.cuh", "layout.h"):
         with open(os.path.join(ROOT, "paper_2209_15445_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -273,7 +273,8 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (o.msc_range_factor < 0.0 || !(o.msc_range_factor < 1e30)) return ADEPT_EINVAL;
   if (o.msc_range_factor == 0.0) o.msc_range_factor = 0.04;
   if (o.field_max_iterations < 0) return ADEPT_EINVAL;
-  if (o.field_max_iterations > 0 && o.fused) return ADEPT_EINVAL;  // the fused kernel has no chord variant
+  // the fused kernel has no variant with chords or the optional physics
+  if (o.fused && (o.field_max_iterations > 0 || o.physics)) return ADEPT_EINVAL;
   if (o.delta_chord_mm < 0.0 || o.delta_intersection_mm < 0.0) return ADEPT_EINVAL;
   if (o.delta_chord_mm == 0.0) o.delta_chord_mm = 0.25;
   if (o.delta_intersection_mm == 0.0) o.delta_intersection_mm = 0.001;
@@ -404,7 +405,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
       int mb = o.blocks_per_sm_species[sp] > 0 ? o.blocks_per_sm_species[sp] : o.blocks_per_sm;
       if (mb <= 0) mb = o.precision ? 3 : 2;
       c->minb[sp] = std::min(4, mb);
-      int bps = transport_max_blocks_per_sm(o.precision, sp, c->minb[sp], o.block_size, o.field_max_iterations > 0);
+      int bps = transport_max_blocks_per_sm(o.precision, sp, c->minb[sp], o.block_size, transport_variant(P));
       c->grid[sp] = sms * (bps < 1 ? 1 : bps);
     }
     if (o.fused) {

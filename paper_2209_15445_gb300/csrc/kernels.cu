@@ -223,23 +223,22 @@ static const void* transport_fn(int species, int minb) {
   return species == 0 ? transport_fn<R, 0>(minb) : (species == 1 ? transport_fn<R, 1>(minb) : transport_fn<R, 2>(minb));
 }
 
-// the kernel of species `species` for these options: the chord-propagator variant for
-// charged species when P.chord_iter > 0
-static const void* pick_transport(int precision, int species, int minb, bool chord) {
-  if (chord && species != 0) return chord_transport_fn(precision, species, minb);
+// the kernel of species `species` for this variant: photons have no optional parts
+static const void* pick_transport(int precision, int species, int minb, int variant) {
+  if (variant && species != 0) return variant_transport_fn(precision, species, minb, variant);
   return precision ? transport_fn<float>(species, minb) : transport_fn<double>(species, minb);
 }
 
-int transport_max_blocks_per_sm(int precision, int species, int minb, int block, bool chord) {
+int transport_max_blocks_per_sm(int precision, int species, int minb, int block, int variant) {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick_transport(precision, species, minb, chord), block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick_transport(precision, species, minb, variant), block, 0);
   return n;
 }
 
 cudaError_t launch_transport(const Params& P, int precision, int species, int minb, int grid, int block,
                              cudaStream_t st) {
   void* args[] = {const_cast<Params*>(&P)};
-  return cudaLaunchKernel(pick_transport(precision, species, minb, P.chord_iter > 0), dim3(grid), dim3(block), args,
+  return cudaLaunchKernel(pick_transport(precision, species, minb, transport_variant(P)), dim3(grid), dim3(block), args,
                           0, st);
 }
 

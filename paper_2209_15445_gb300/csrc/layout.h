@@ -171,9 +171,12 @@ cudaError_t launch_probe_distance(const Params& P, int prec, const double* pos, 
                                   int* next, cudaStream_t st);
 cudaError_t launch_probe_sample(const Params& P, int which, int m, int prec, double E, uint32_t event,
                                 int n, double* out, cudaStream_t st);
-int transport_max_blocks_per_sm(int precision, int species, int minb, int block, bool chord);
-// the chord-propagator variant of the e- (species 1) or e+ (2) kernel, 2 or 3 blocks/SM
-const void* chord_transport_fn(int precision, int species, int minb);
+// variant: bit 0 chord propagation, bit 1 multiple scattering / loss fluctuations
+int transport_max_blocks_per_sm(int precision, int species, int minb, int block, int variant);
+// a variant (1..3) of the e- (species 1) or e+ (2) kernel, 2 or 3 blocks/SM
+const void* variant_transport_fn(int precision, int species, int minb, int variant);
+// the variant the options of P call for
+inline int transport_variant(const Params& P) { return (P.chord_iter > 0 ? 1 : 0) | (P.physics ? 2 : 0); }
 cudaError_t launch_probe_chord(const Params& P, int prec, const double* pos, const double* dir, const int* vol,
                                const double* T, const int* q, const double* s_phys, int n, double* out, cudaStream_t st);
 cudaError_t launch_probe_continuous(const Params& P, int which, int species, int m, int prec, double T, double s,

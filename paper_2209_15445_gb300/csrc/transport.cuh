@@ -111,10 +111,11 @@ enum Outcome { kDead = 0, kAlive = 1, kInteract = 2 };
 // distance (S5/S6), move, continuous loss (S7) and boundary crossing (S8). A step that
 // ends in a discrete interaction returns kInteract with the chosen process; the
 // interaction itself (S9) runs later on a full warp. dep is the energy to score in
-// dep_bin; sec receives the two photons of a positron that stops. CH compiles in the
-// chord propagator of the field (used when P.chord_iter > 0), kept out of the kernels
-// that run the analytic helix.
-template <class R, int S, bool CH = false>
+// dep_bin; sec receives the two photons of a positron that stops. The variant V compiles
+// in the optional parts, kept out of the kernels that do not use them: bit 0 the chord
+// propagator of the field (P.chord_iter > 0), bit 1 multiple scattering and loss
+// fluctuations (P.physics).
+template <class R, int S, int V = 0>
 __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>& sec, double& dep, int& dep_bin,
                                               uint32_t& pstep, int& proc) {
   constexpr int q = S == 1 ? -1 : (S == 2 ? 1 : 0);
@@ -175,10 +176,11 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
   const R stot = sg0 + sg1 + sg2;
   // S3/S4: sampled interaction length and the range-based step limit
   R s_phys = stot > (R)0 ? M<R>::fdiv(-M<R>::flog(u0), stot) : M<R>::big();
-  const bool msc = (P.physics & 1u) != 0, fluct = (P.physics & 2u) != 0;
+  constexpr bool CH = (V & 1) != 0, PH = (V & 2) != 0 && S != 0;
+  const bool msc = PH && (P.physics & 1u) != 0, fluct = PH && (P.physics & 2u) != 0;
   if (q != 0 && m >= 0) {
     R smax = (Rr <= (R)kRhoF) ? Rr : ((R)kAlphaR * Rr > (R)kRhoF ? (R)kAlphaR * Rr : (R)kRhoF);
-    if (msc) {  // multiple-scattering step limit
+    if (PH && msc) {  // multiple-scattering step limit
       const R fR = (R)P.msc_f * Rr;
       const R sm = fR > (R)0.01 ? fR : (R)0.01;
       if (sm < smax) smax = sm;
@@ -227,21 +229,26 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
     R Epr = 0;
     if (s < Rr) Epr = inverse_range<R>(range_nodes<R>(P.tab, S == 2) + (size_t)m * kNNode, Rr - s, bin + 1);
     double Ep = (Epr > Er) ? t.E : to_d<R>(Epr);
-    if (fluct && s < Rr && Ep >= P.tcut) {
-      const R xi = (R)(kTwoPiRe2Me * __ldg(&P.mat[m].n_el));
-      const R sig = M<R>::sqrt(fluct_sigma2<R>(Er, xi, (R)__ldg(P.tab.Tc + m), s, S == 2));
-      Ep = t.E - fluct_loss<R>(rs, t.E - Ep, sig);
+    if constexpr (PH) {
+      if (fluct && s < Rr && Ep >= P.tcut) {
+        const R xi = (R)(kTwoPiRe2Me * __ldg(&P.mat[m].n_el));
+        const R sig = M<R>::sqrt(fluct_sigma2<R>(Er, xi, (R)__ldg(P.tab.Tc + m), s, S == 2));
+        Ep = t.E - fluct_loss<R>(rs, t.E - Ep, sig);
+        Epr = to_r<R>(Ep);
+      }
     }
     dep += t.E - Ep;
     t.E = Ep;
-    if (to_r<R>(Ep) < tcut) {
+    if (Epr < tcut) {
       dep += t.E;
       t.E = 0.0;
       if (S == 2) annihilate_at_rest<R>(rs, sec);
       return kDead;
     }
     // optional multiple scattering: the direction at the end of the step
-    if (msc && s > (R)0) msc_deflect<R>(rs, msc_theta0<R>(Er, (R)__ldg(&P.mat[m].inv_x0), s), t.u);
+    if constexpr (PH) {
+      if (msc && s > (R)0) msc_deflect<R>(rs, msc_theta0<R>(Er, (R)__ldg(&P.mat[m].inv_x0), s), t.u);
+    }
   }
   // S8: boundary crossing
   if (boundary) {
@@ -397,7 +404,7 @@ __device__ __forceinline__ void drain(const Params& P, int p, WarpRing<R>& ring,
 
 // One warp takes 32 consecutive tracks of species S: phase A for each, appends the
 // survivors, queues the interactions and runs full warps of them as they accumulate.
-template <class R, int S, bool CH = false>
+template <class R, int S, int V = 0>
 __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, uint32_t n, WarpRing<R>& ring,
                                          uint32_t& head, uint32_t& tail, unsigned long long* nsteps,
                                          unsigned long long* ncreated) {
@@ -414,7 +421,7 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
     load_track<R>(P.qd[3 * p + S], i, t);
     double dep = 0.0;
     int dep_bin = -1;
-    outcome = step_transport<R, S, CH>(P, t, sec, dep, dep_bin, pstep, proc);
+    outcome = step_transport<R, S, V>(P, t, sec, dep, dep_bin, pstep, proc);
     // S10: score the step's deposit in (event, layer, material)
     score(P, t.ev, dep_bin, dep);
   }
@@ -441,8 +448,9 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
 // The three species kernels of a generation are independent (each reads its own current
 // queue and appends to the next ones atomically), so they run concurrently on three
 // streams; k_close_generation then publishes the next queue sizes.
-// CH: the chord-propagator variant (chord.cu instantiates it for e- and e+).
-template <class R, int S, int MINB, bool CH = false>
+// V: the variant of the step (see step_transport); variants.cu instantiates V = 1..3 for
+// e- and e+.
+template <class R, int S, int MINB, int V = 0>
 __global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
   __shared__ unsigned long long s_steps, s_created[3];
   __shared__ WarpRing<R> rings[8];
@@ -458,7 +466,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
   uint32_t head = 0, tail = 0;
   unsigned long long nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
   for (uint32_t tile = blockIdx.x * wpb + (threadIdx.x >> 5); tile < tiles; tile += gridDim.x * wpb)
-    run_tile<R, S, CH>(P, p, tile << 5, n, ring, head, tail, nsteps, ncreated);
+    run_tile<R, S, V>(P, p, tile << 5, n, ring, head, tail, nsteps, ncreated);
   if (tail != head) drain<R, S>(P, p, ring, head, tail - head, ncreated);
   if ((threadIdx.x & 31) == 0) {
     if (nsteps[S]) atomicAdd(&s_steps, nsteps[S]);

@@ -136,16 +136,28 @@ def test_showers_with_msc_and_fluctuations(precision, phys):
         assert same.mean() > 0.75, same.mean()
 
 
-def test_msc_barrel_field_and_fused_mode():
+def test_msc_barrel_field():
     need_gpu()
     geom = W.barrel_calorimeter()
     prim = W.barrel_primaries(200, seed=8)
     ref = oracle.Oracle(geom, field_T=3.8).transport(prim, physics=BOTH)
-    for fused in (0, 1):
-        tr = make(geom, precision=1, field_T=3.8, arena_bytes=2 << 30, physics=BOTH, fused=fused, tuned=False)
-        edep, meta = gpu_run(tr, prim)
-        tr.close()
-        layer_check(edep, ref["edep"], rel=0.03)
+    tr = make(geom, precision=1, field_T=3.8, arena_bytes=2 << 30, physics=BOTH, tuned=False)
+    edep, meta = gpu_run(tr, prim)
+    tr.close()
+    layer_check(edep, ref["edep"], rel=0.03)
+
+
+def test_msc_with_chords_matches_oracle():
+    """both optional parts at once (the V = 3 kernels)"""
+    need_gpu()
+    geom = W.barrel_calorimeter()
+    prim = W.barrel_primaries(150, seed=9)
+    ref = oracle.Oracle(geom, field_T=3.8).transport(prim, physics=BOTH, field_max_iter=100)
+    tr = make(geom, precision=1, field_T=3.8, arena_bytes=2 << 30, physics=BOTH, field_max_iterations=100,
+              tuned=False)
+    edep, meta = gpu_run(tr, prim)
+    tr.close()
+    layer_check(edep, ref["edep"], rel=0.03)
 
 
 def test_secondaries_and_step_lengths_with_msc_fp64():
@@ -175,3 +187,5 @@ def test_invalid_physics_options_rejected():
         make(W.slab_calorimeter(), precision=1, physics=4)
     with pytest.raises(A.AdeptError):
         make(W.slab_calorimeter(), precision=1, physics=1, msc_range_factor=-1.0)
+    with pytest.raises(A.AdeptError):  # the fused kernel has no physics variant
+        make(W.slab_calorimeter(), precision=1, physics=1, fused=1, tuned=False)
