@@ -95,6 +95,7 @@ def lib():
             L.or_msc_theta0.argtypes = [p, i, d, d]; L.or_msc_theta0.restype = d
             L.or_chord_step.argtypes = [p, d, i, d, i, d, d, dp, dp, i, ip, dp, ip]
             L.or_chord_step.restype = i
+            L.or_raytrace.argtypes = [p, dp, i, i, dp]
             L.or_fluct_sigma2.argtypes = [p, i, d, d, i]; L.or_fluct_sigma2.restype = d
             L.or_n_volumes.argtypes = [p]; L.or_n_volumes.restype = i
             L.or_n_bins.argtypes = [p]; L.or_n_bins.restype = i
@@ -205,6 +206,13 @@ class Oracle:
         return out
 
     def msc_theta0(self, m, T, s): return lib().or_msc_theta0(self.h, m, T, s)
+
+    def raytrace(self, cam, nx, ny):
+        """(ny, nx, 2) image: mass thickness (g/cm^2) and volumes entered per pixel"""
+        cam = np.ascontiguousarray(cam, np.float64)
+        out = np.zeros((ny, nx, 2))
+        lib().or_raytrace(self.h, _dp(cam), nx, ny, _dp(out))
+        return out
 
     def chord_step(self, T, q, s_phys, max_iter, pos, d, vol, delta_chord=0.25, delta_int=0.001):
         """(status, position, direction, next, path, iterations) of one chord-propagated step"""

@@ -696,6 +696,92 @@ double or_helix_distance(const or_ctx* c, double T, int q, const double p[3], co
   return s;
 }
 
+/* ------------------------------------------------------------------ ray tracing */
+static void normalize3(double v[3]);
+/* entry of the ray p + t u (t >= 0) into the world, snapped onto the entry face; returns
+ * 0 if the ray misses it */
+static int world_entry(const or_ctx* c, const double p[3], const double u[3], double q[3]) {
+  double t0 = 0.0, t1 = kInf;
+  int face = -1; /* 0/1/2: axis of the entry plane (box) or z cap; 3: the cylinder */
+  double fval = 0.0;
+  if (c->kind == 0) {
+    const double lo[3] = {-c->half_xy, -c->half_xy, c->bnd[0]};
+    const double hi[3] = {c->half_xy, c->half_xy, c->bnd[c->n_vol]};
+    for (int a = 0; a < 3; ++a) {
+      if (u[a] == 0.0) {
+        if (p[a] < lo[a] || p[a] > hi[a]) return 0;
+        continue;
+      }
+      double ta = (lo[a] - p[a]) / u[a], tb = (hi[a] - p[a]) / u[a];
+      double va = lo[a], vb = hi[a];
+      if (ta > tb) { double x = ta; ta = tb; tb = x; x = va; va = vb; vb = x; }
+      if (ta > t0) { t0 = ta; face = a; fval = va; }
+      if (tb < t1) t1 = tb;
+    }
+  } else {
+    const double R = c->bnd[c->n_vol - 1];
+    const double a = u[0] * u[0] + u[1] * u[1], b = p[0] * u[0] + p[1] * u[1];
+    const double cc = p[0] * p[0] + p[1] * p[1] - R * R;
+    if (a > 0.0) {
+      const double D = b * b - a * cc;
+      if (D < 0.0) return 0;
+      const double sq = sqrt(D);
+      const double ta = (-b - sq) / a, tb = (-b + sq) / a;
+      if (ta > t0) { t0 = ta; face = 3; }
+      if (tb < t1) t1 = tb;
+    } else if (cc > 0.0) {
+      return 0;
+    }
+    if (u[2] != 0.0) {
+      double ta = (-c->half_z - p[2]) / u[2], tb = (c->half_z - p[2]) / u[2];
+      double va = -c->half_z, vb = c->half_z;
+      if (ta > tb) { double x = ta; ta = tb; tb = x; x = va; va = vb; vb = x; }
+      if (ta > t0) { t0 = ta; face = 2; fval = va; }
+      if (tb < t1) t1 = tb;
+    } else if (fabs(p[2]) > c->half_z) {
+      return 0;
+    }
+  }
+  if (!(t0 <= t1)) return 0;
+  for (int a = 0; a < 3; ++a) q[a] = p[a] + t0 * u[a];
+  if (face >= 0 && face < 3) q[face] = fval;
+  if (face == 3) {
+    const double R = c->bnd[c->n_vol - 1], r = sqrt(q[0] * q[0] + q[1] * q[1]);
+    if (r > 0.0) { q[0] *= R / r; q[1] *= R / r; }
+  }
+  return 1;
+}
+
+void or_raytrace(const or_ctx* c, const double cam[11], int nx, int ny, double* out) {
+  double d[3] = {cam[3], cam[4], cam[5]}, up[3] = {cam[6], cam[7], cam[8]};
+  normalize3(d);
+  double rt[3] = {d[1] * up[2] - d[2] * up[1], d[2] * up[0] - d[0] * up[2], d[0] * up[1] - d[1] * up[0]};
+  normalize3(rt);
+  const double u2[3] = {rt[1] * d[2] - rt[2] * d[1], rt[2] * d[0] - rt[0] * d[2], rt[0] * d[1] - rt[1] * d[0]};
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const double a = ((i + 0.5) / nx - 0.5) * cam[9], b = ((j + 0.5) / ny - 0.5) * cam[10];
+      const double p[3] = {cam[0] + a * rt[0] + b * u2[0], cam[1] + a * rt[1] + b * u2[1],
+                           cam[2] + a * rt[2] + b * u2[2]};
+      double q[3], mass = 0.0, n = 0.0;
+      if (world_entry(c, p, d, q)) {
+        int vol = or_locate(c, q, d);
+        for (int k = 0; vol >= 0 && k < 100000; ++k) {
+          n += 1.0;
+          int next;
+          const double s = or_distance(c, q, d, vol, &next);
+          const int m = c->vol_mat[vol];
+          if (m >= 0) mass += c->mat[m].rho * s * 0.1;
+          for (int e = 0; e < 3; ++e) q[e] += s * d[e];
+          if (c->kind == 0 && next >= 0) q[2] = c->bnd[d[2] > 0.0 ? vol + 1 : vol];
+          vol = next;
+        }
+      }
+      out[2 * ((size_t)j * nx + i)] = mass;
+      out[2 * ((size_t)j * nx + i) + 1] = n;
+    }
+}
+
 /* ------------------------------------------------------------------ chord propagation */
 /* is p inside (or on the boundary of) volume vol */
 static int inside_volume(const or_ctx* c, const double p[3], int vol) {

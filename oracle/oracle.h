@@ -135,6 +135,16 @@ int or_chord_step(const or_ctx* c, double T, int q, double s_phys, int max_iter,
                   double delta_int, double p[3], double u[3], int vol, int* next, double* s_done,
                   int* iters);
 
+/* ---- ray tracing of the geometry (paper Sec. 2.1: navigation validated on ray-traced
+ * images, GPU against CPU and single against double precision) ----
+ * Orthographic camera cam = {origin[3], view direction[3], up[3], width, height} (mm): the
+ * ray of pixel (i, j) starts at origin + ((i+0.5)/nx - 0.5) width right + ((j+0.5)/ny - 0.5)
+ * height up', right = dir x up / |.|, up' = right x dir, and runs along dir. It enters the
+ * world (box or cylinder) analytically, snapped onto the face it enters, and then crosses
+ * volume after volume with or_distance. out[2 (j nx + i) + {0, 1}] = the mass thickness it
+ * traverses (g/cm^2) and the number of volumes it enters (0: it misses the world). */
+void or_raytrace(const or_ctx* c, const double cam[11], int nx, int ny, double* out);
+
 /* ---- transport ---- */
 typedef struct {
   uint32_t seed;
