@@ -70,7 +70,7 @@ def args_parse():
     ap.add_argument("--arena-gb", type=float, default=10.0)
     ap.add_argument("--bps", type=int, default=0, help="transport-kernel blocks/SM variant (0 = library default)")
     ap.add_argument("--bps-species", type=str, default="", help="per-species variants gamma,e-,e+")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "rt"],
                     help="c2 (default) is the headline line; the others are the configuration studies")
     ap.add_argument("--seconds", type=float, default=20.0, help="serving workload duration")
     ap.add_argument("--genlog", default="", help="write the per-generation queue sizes of the last step here")
@@ -378,6 +378,46 @@ def run_study(a):
 
     B.build()
     torch.cuda.set_device(0)
+    if a.workload == "rt":
+        # ray-traced images of the barrel (paper Sec. 2.1: single against double precision
+        # navigation), 4096 x 4096 side view into device memory, and the CPU oracle on a
+        # 256 x 256 image of the same view
+        import oracle
+        geom = W.barrel_calorimeter()
+        cam = [-4000.0, 0.0, 0.0, 1.0, 0.05, 0.02, 0, 0, 1, 3800.0, 6500.0]
+        nx = ny = 4096
+        tr = A.Transport(geom, precision=1, field_T=3.8, arena_bytes=1 << 30)
+        dev = torch.empty(nx * ny * 2, dtype=torch.float64, device="cuda")
+        res = {}
+        for prec in (0, 1):
+            for _ in range(max(1, a.warmup)):
+                A.adept_raytrace_device(tr.h, prec, cam, nx, ny, dev.data_ptr())
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tr.stream.synchronize()
+            e0.record(tr.stream)
+            for _ in range(a.steps):
+                assert A.adept_raytrace_device(tr.h, prec, cam, nx, ny, dev.data_ptr()) == 0
+            e1.record(tr.stream)
+            tr.stream.synchronize()
+            ms = e0.elapsed_time(e1) / a.steps
+            crossings = float(dev.view(ny, nx, 2)[..., 1].sum())
+            res["fp32" if prec else "fp64"] = {"ms": ms, "rays_per_s": nx * ny / (ms / 1e3),
+                                                "crossings_per_s": crossings / (ms / 1e3)}
+        tr.close()
+        o = oracle.Oracle(geom, field_T=3.8)
+        t0 = time.perf_counter()
+        o.raytrace(cam, 256, 256)
+        cpu = 256 * 256 / (time.perf_counter() - t0)
+        line = {"metric": "ray-traced pixels/s (geometry validation)", "value": res["fp32"]["rays_per_s"],
+                "unit": "pixels/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": res["fp32"]["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 distances / f64 positions", "data": "synthetic",
+                "config": {"workload": "4096 x 4096 orthographic side view of the 20-layer barrel"},
+                "fp64": res["fp64"], "fp32": res["fp32"], "fp32_over_fp64": res["fp32"]["rays_per_s"] / res["fp64"]["rays_per_s"],
+                "cpu_baseline": {"value": cpu, "unit": "pixels/s", "cores": 1, "kind": "oracle",
+                                 "sample": "256 x 256 image of the same view, FP64 C oracle, one thread"}}
+        print(json.dumps(line))
+        return
     if a.workload == "c1":
         # plain FP64, one event per transport, one generation per launch with the queue
         # sizes read back after each (the paper's small-batch form)

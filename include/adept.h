@@ -303,6 +303,20 @@ int adept_probe_chord(adept_ctx* ctx, int32_t prec, const double* host_pos, cons
                       const int32_t* host_vol, const double* host_T, const int32_t* host_charge,
                       const double* host_s_phys, size_t n, double* host_out);
 
+/* Ray-traced image of the geometry (paper Sec. 2.1: navigation validated on ray-traced
+ * images, GPU against CPU and single against double precision). Orthographic camera
+ * cam = {origin[3], view direction[3], up[3], width, height} (mm): the ray of pixel (i, j)
+ * starts at origin + ((i+0.5)/nx - 0.5) width right + ((j+0.5)/ny - 0.5) height up' (right =
+ * dir x up normalised, up' = right x dir) and runs along dir; it enters the world
+ * analytically and crosses volume after volume with the transport's navigation, with FP64
+ * (prec 0) or FP32 (prec 1) distances. out[2 (j nx + i) + {0, 1}] = mass thickness traversed
+ * (g/cm^2) and volumes entered (0: the ray misses the world). out is host memory
+ * (out_on_device 0; synchronous, the image is made and copied in bands) or caller-owned
+ * device memory of 16 nx ny bytes (out_on_device 1; one launch on the context's stream, not
+ * waited for). */
+int adept_raytrace(adept_ctx* ctx, int32_t prec, const double cam[11], int32_t nx, int32_t ny, double* out,
+                   int32_t out_on_device);
+
 /* Table build without any allocation, for callers that cannot allocate device memory:
  * code that runs under a host framework which owns every device allocation (a fixed
  * device budget handed out by someone else), or that must not add an allocation, with its

@@ -128,6 +128,7 @@ def load(path: str = LIB_PATH):
             "adept_probe_distance": [vp, i32, dp, dp, i32p, dp, i32p, sz, dp, i32p],
             "adept_probe_sample": [vp, i32, i32, i32, C.c_double, u32, sz, dp],
             "adept_probe_continuous": [vp, i32, i32, i32, i32, C.c_double, C.c_double, u32, sz, dp],
+            "adept_raytrace": [vp, i32, dp, i32, i32, C.c_void_p, i32],
             "adept_probe_chord": [vp, i32, dp, dp, C.POINTER(C.c_int32), dp, C.POINTER(C.c_int32), dp, sz, dp],
             "adept_build_tables_noalloc": [C.POINTER(adept_material), i32, C.c_double, vp, vp, vp],
         }
@@ -281,6 +282,20 @@ def adept_probe_sample(h, which, m, prec, E, event, n):
     out = np.zeros((n, 12))
     rc = load().adept_probe_sample(h, which, m, prec, E, event, n, _dp(out))
     return rc, out
+
+
+def adept_raytrace(h, prec, cam, nx, ny):
+    """(rc, (ny, nx, 2) image in host memory): mass thickness (g/cm^2), volumes entered"""
+    cam = np.ascontiguousarray(cam, np.float64)
+    out = np.zeros((ny, nx, 2))
+    rc = load().adept_raytrace(h, prec, _dp(cam), nx, ny, out.ctypes.data_as(C.c_void_p), 0)
+    return rc, out
+
+
+def adept_raytrace_device(h, prec, cam, nx, ny, dev_ptr):
+    """launch into caller-owned device memory (16 nx ny bytes) on the context's stream"""
+    cam = np.ascontiguousarray(cam, np.float64)
+    return load().adept_raytrace(h, prec, _dp(cam), nx, ny, C.c_void_p(dev_ptr), 1)
 
 
 def adept_get_leaked(h, rid):

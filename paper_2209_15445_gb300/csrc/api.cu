@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
@@ -1105,6 +1106,46 @@ extern "C" int adept_probe_sample(adept_ctx* c, int32_t which, int32_t m, int32_
   CK(launch_probe_sample(c->P, which, m, prec, E, event, (int)n, dout, c->stream));
   CK(cudaMemcpyAsync(host_out, dout, 96 * n, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  return ADEPT_OK;
+}
+
+extern "C" int adept_raytrace(adept_ctx* c, int32_t prec, const double cam[11], int32_t nx, int32_t ny, double* out,
+                              int32_t out_on_device) {
+  if (!c || !cam || (prec != 0 && prec != 1) || nx < 0 || ny < 0 || (nx && ny && !out)) return ADEPT_EINVAL;
+  if ((long long)nx * ny > (1ll << 31)) return fail(c, ADEPT_EINVAL, "at most 2^31 pixels");
+  // the camera frame, as the CPU reference builds it
+  RayCam k{};
+  double d[3] = {cam[3], cam[4], cam[5]}, up[3] = {cam[6], cam[7], cam[8]};
+  auto norm = [](double* v) {
+    const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= n; v[1] /= n; v[2] /= n;
+    return n > 0.0 && std::isfinite(n);
+  };
+  if (!norm(d)) return fail(c, ADEPT_EINVAL, "camera view direction is zero");
+  double rt[3] = {d[1] * up[2] - d[2] * up[1], d[2] * up[0] - d[0] * up[2], d[0] * up[1] - d[1] * up[0]};
+  if (!norm(rt)) return fail(c, ADEPT_EINVAL, "camera up vector is parallel to the view direction");
+  for (int a = 0; a < 3; ++a) { k.o[a] = cam[a]; k.d[a] = d[a]; k.right[a] = rt[a]; }
+  k.up[0] = rt[1] * d[2] - rt[2] * d[1];
+  k.up[1] = rt[2] * d[0] - rt[0] * d[2];
+  k.up[2] = rt[0] * d[1] - rt[1] * d[0];
+  k.width = cam[9];
+  k.height = cam[10];
+  if (!nx || !ny) return ADEPT_OK;
+  if (out_on_device) {
+    CK(launch_raytrace(c->P, prec, k, nx, ny, 0, ny, out, c->stream));
+    return ADEPT_OK;
+  }
+  // host output: bands of rows through the probe buffer
+  if (16 * (size_t)nx > c->probe_bytes)
+    return fail(c, ADEPT_EINVAL, "rows wider than %zu pixels need device output", c->probe_bytes / 16);
+  double* dout = reinterpret_cast<double*>(c->probe);
+  const int rows = (int)std::max<size_t>(1, c->probe_bytes / (16 * (size_t)nx));
+  for (int j0 = 0; j0 < ny; j0 += rows) {
+    const int nr = std::min(rows, ny - j0);
+    CK(launch_raytrace(c->P, prec, k, nx, ny, j0, nr, dout, c->stream));
+    CK(cudaMemcpyAsync(out + 2 * (size_t)j0 * nx, dout, 16 * (size_t)nx * nr, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
   return ADEPT_OK;
 }
 

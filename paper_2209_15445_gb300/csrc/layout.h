@@ -177,6 +177,14 @@ int transport_max_blocks_per_sm(int precision, int species, int minb, int block,
 const void* variant_transport_fn(int precision, int species, int minb, int variant);
 // the variant the options of P call for
 inline int transport_variant(const Params& P) { return (P.chord_iter > 0 ? 1 : 0) | (P.physics ? 2 : 0); }
+// orthographic camera of the ray tracer: the image centre, the unit right, up and view vectors
+struct RayCam {
+  double o[3], right[3], up[3], d[3];
+  double width, height;
+};
+// rows [row0, row0 + rows) of an nx x ny image into out (16 bytes per pixel)
+cudaError_t launch_raytrace(const Params& P, int prec, const RayCam& cam, int nx, int ny, int row0, int rows,
+                            double* out, cudaStream_t st);
 cudaError_t launch_probe_chord(const Params& P, int prec, const double* pos, const double* dir, const int* vol,
                                const double* T, const int* q, const double* s_phys, int n, double* out, cudaStream_t st);
 cudaError_t launch_probe_continuous(const Params& P, int which, int species, int m, int prec, double T, double s,
