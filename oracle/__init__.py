@@ -71,7 +71,7 @@ def lib():
             L.or_u01_f64.argtypes = [u32, u32]; L.or_u01_f64.restype = d
             L.or_u01_f32.argtypes = [u32]; L.or_u01_f32.restype = C.c_float
             L.or_child_id.argtypes = [u32, u32, u64, u32, u32]; L.or_child_id.restype = u64
-            L.or_create.argtypes = [i, ip, dp, dp, dp, i, i, i, ip, dp, d, d, dp, d, d, d]
+            L.or_create.argtypes = [i, ip, dp, dp, dp, ip, ip, dp, dp, i, i, i, ip, dp, d, d, dp, d, d, d]
             L.or_create.restype = p
             L.or_destroy.argtypes = [p]
             for name in ("or_mu_compton", "or_mu_pair", "or_mu_photo", "or_lambda_annih",
@@ -154,11 +154,18 @@ class Oracle:
         A = np.array([m.A for m in mats], np.float64)
         rho = np.array([m.density for m in mats], np.float64)
         I = np.array([m.I_eV for m in mats], np.float64)
+        # compounds: their elements (Z, A, atoms per formula unit), material after material
+        ne = np.array([len(getattr(m, "elements", ())) for m in mats], np.int32)
+        els = [e for m in mats for e in getattr(m, "elements", ())] or [(0, 0.0, 0.0)]
+        eZ = np.array([e[0] for e in els], np.int32)
+        eA = np.array([e[1] for e in els], np.float64)
+        en = np.array([e[2] for e in els], np.float64)
         sm = np.array(geom.sub_materials, np.int32)
         st = np.array(geom.sub_thickness, np.float64)
         lr = np.array(geom.layer_r if geom.layer_r else [0.0], np.float64)
-        self._keep = (Z, A, rho, I, sm, st, lr)
-        self.h = L.or_create(self.n_mat, _ip(Z), _dp(A), _dp(rho), _dp(I), geom.kind, geom.n_layers,
+        self._keep = (Z, A, rho, I, ne, eZ, eA, en, sm, st, lr)
+        self.h = L.or_create(self.n_mat, _ip(Z), _dp(A), _dp(rho), _dp(I), _ip(ne), _ip(eZ), _dp(eA), _dp(en),
+                             geom.kind, geom.n_layers,
                              len(sm), _ip(sm), _dp(st), geom.half_xy, geom.half_z, _dp(lr),
                              range_cut_mm, field_T, tracking_cut_MeV)
         if not self.h:

@@ -112,8 +112,12 @@ static double stream_u(stream_t* s) {
 
 /* ------------------------------------------------------------------ context */
 typedef struct {
-  int Z;
+  int Z;               /* > 0 for matter (a compound's mean Z); 0 vacuum */
   double A, rho, I;
+  int n_elem;          /* elements: Z, A, atoms per mm^3 */
+  int eZ[OR_MAX_ELEM];
+  double eA[OR_MAX_ELEM], en_at[OR_MAX_ELEM];
+  double ZoA;          /* <Z/A> by mass */
   double n_at, n_el;   /* 1/mm^3 */
   double invX0;        /* 1/mm */
   double Cbar, x0, x1, a_d; /* Sternheimer-Peierls density effect */
@@ -171,15 +175,21 @@ double or_mu_compton(const or_ctx* c, int m, double E) {
  * 1/X0 = 4 alpha re^2 (NA rho / A) [Z^2 (Lrad - f(Z)) + Z L'rad],
  * Lrad = ln(184.15 Z^-1/3), L'rad = ln(1194 Z^-2/3), f = Davies-Bethe-Maximon Coulomb
  * correction a^2[(1+a^2)^-1 + 0.20206 - 0.0369 a^2 + 0.0083 a^4 - 0.002 a^6], a = alpha Z. */
-static double inv_x0(const mat_t* t) {
-  const double Z = t->Z;
+static double inv_x0_per_atom(double Z) {
   const double lz = log(Z);
   const double Lrad = log(184.15) - lz / 3.0;
   const double Lp = log(1194.0) - 2.0 * lz / 3.0;
   const double a2 = (kAlpha * Z) * (kAlpha * Z);
   const double f = a2 * (1.0 / (1.0 + a2) + 0.20206 - 0.0369 * a2 + 0.0083 * a2 * a2 -
                          0.002 * a2 * a2 * a2);
-  return 4.0 * kAlpha * kRe * kRe * t->n_at * (Z * Z * (Lrad - f) + Z * Lp);
+  return 4.0 * kAlpha * kRe * kRe * (Z * Z * (Lrad - f) + Z * Lp);
+}
+/* a compound adds its elements' terms by atom density: 1/X0 = sum_i w_i / X0_i (Bragg
+ * additivity, as the PDG gives it for mixtures) */
+static double inv_x0(const mat_t* t) {
+  double s = 0.0;
+  for (int i = 0; i < t->n_elem; ++i) s += t->en_at[i] * inv_x0_per_atom(t->eZ[i]);
+  return s;
 }
 double or_inv_X0(const or_ctx* c, int m) { return c->mat[m].invX0; }
 
@@ -199,16 +209,21 @@ double or_mu_pair(const or_ctx* c, int m, double E) {
  * sigma = 4 sqrt(2) alpha^4 Z^5 sigma_Th (m/E)^(7/2), no edges. */
 double or_mu_photo(const or_ctx* c, int m, double E) {
   const double q = kMe / E;
-  const double Z = c->mat[m].Z;
   const double sth = 8.0 * kPi / 3.0 * kRe * kRe;
   const double a4 = kAlpha * kAlpha * kAlpha * kAlpha;
-  return c->mat[m].n_at * 4.0 * sqrt(2.0) * a4 * (Z * Z * Z * Z * Z) * sth * (q * q * q * sqrt(q));
+  const mat_t* t = &c->mat[m];
+  double s = 0.0; /* a compound: the sum over its atoms */
+  for (int i = 0; i < t->n_elem; ++i) {
+    const double Z = t->eZ[i];
+    s += t->en_at[i] * 4.0 * sqrt(2.0) * a4 * (Z * Z * Z * Z * Z) * sth * (q * q * q * sqrt(q));
+  }
+  return s;
 }
 
 /* Sternheimer & Peierls (Phys. Rev. B 3 (1971) 3681) general density-effect
  * parameterisation for condensed media from I, rho and Z/A. */
 static void density_params(mat_t* t) {
-  const double hwp = 28.816 * sqrt(t->rho * t->Z / t->A); /* eV */
+  const double hwp = 28.816 * sqrt(t->rho * t->ZoA); /* eV */
   t->Cbar = 2.0 * log(t->I / hwp) + 1.0;
   if (t->I < 100.0) {
     t->x1 = 2.0;
@@ -1268,22 +1283,58 @@ void or_sample(const or_ctx* c, int which, int m, double E, uint32_t seed, uint3
 
 /* ------------------------------------------------------------------ setup */
 or_ctx* or_create(int n_mat, const int* mat_Z, const double* mat_A, const double* mat_rho,
-                  const double* mat_I_eV, int kind, int n_layers, int n_sub, const int* sub_mat,
+                  const double* mat_I_eV, const int* mat_n_elem, const int* elem_Z, const double* elem_A,
+                  const double* elem_atoms, int kind, int n_layers, int n_sub, const int* sub_mat,
                   const double* sub_thick, double half_xy, double half_z, const double* layer_r,
                   double range_cut_mm, double field_T, double tracking_cut_MeV) {
   if (n_mat <= 0 || n_mat > OR_MAX_MAT || n_layers <= 0 || n_sub <= 0) return NULL;
   or_ctx* c = (or_ctx*)calloc(1, sizeof(or_ctx));
   if (!c) return NULL;
   c->n_mat = n_mat;
+  int e0 = 0; /* first element of material m */
   for (int m = 0; m < n_mat; ++m) {
     mat_t* t = &c->mat[m];
     t->Z = mat_Z[m];
     t->A = mat_A[m];
     t->rho = mat_rho[m];
     t->I = mat_I_eV[m];
-    if (t->Z > 0) {
+    const int ne = mat_n_elem ? mat_n_elem[m] : 0;
+    if (ne < 0 || ne > OR_MAX_ELEM) { free(c); return NULL; }
+    if (ne > 0) {
+      /* a compound: atoms per mm^3 of each element from the formula's mass fractions */
+      double M = 0.0, natoms = 0.0, zsum = 0.0;
+      for (int i = 0; i < ne; ++i) {
+        M += elem_atoms[e0 + i] * elem_A[e0 + i];
+        natoms += elem_atoms[e0 + i];
+        zsum += elem_atoms[e0 + i] * elem_Z[e0 + i];
+      }
+      t->n_elem = ne;
+      t->ZoA = 0.0;
+      t->n_at = 0.0;
+      t->n_el = 0.0;
+      for (int i = 0; i < ne; ++i) {
+        const double w = elem_atoms[e0 + i] * elem_A[e0 + i] / M;
+        t->eZ[i] = elem_Z[e0 + i];
+        t->eA[i] = elem_A[e0 + i];
+        t->en_at[i] = kNA * t->rho * w / elem_A[e0 + i] * 1e-3;
+        t->ZoA += w * elem_Z[e0 + i] / elem_A[e0 + i];
+        t->n_at += t->en_at[i];
+        t->n_el += elem_Z[e0 + i] * t->en_at[i];
+      }
+      t->A = M / natoms;
+      t->Z = (int)(zsum / natoms + 0.5);
+      if (t->Z < 1) t->Z = 1;
+      e0 += ne;
+    } else if (t->Z > 0) {
       t->n_at = kNA * t->rho / t->A * 1e-3;
       t->n_el = t->Z * t->n_at;
+      t->n_elem = 1;
+      t->eZ[0] = t->Z;
+      t->eA[0] = t->A;
+      t->en_at[0] = t->n_at;
+      t->ZoA = t->Z / t->A;
+    }
+    if (t->Z > 0) {
       t->invX0 = inv_x0(t);
       density_params(t);
     }
@@ -1334,7 +1385,7 @@ or_ctx* or_create(int n_mat, const int* mat_Z, const double* mat_A, const double
     c->n_vol = v;
   }
   for (int v = 0; v < c->n_vol; ++v)
-    if (c->vol_mat[v] >= 0 && mat_Z[c->vol_mat[v]] <= 0) { c->vol_mat[v] = -1; c->vol_bin[v] = -1; }
+    if (c->vol_mat[v] >= 0 && c->mat[c->vol_mat[v]].Z <= 0) { c->vol_mat[v] = -1; c->vol_bin[v] = -1; }
   c->n_bins = n_layers * n_sub;
   build_tables(c, range_cut_mm);
   return c;

@@ -35,6 +35,7 @@ extern "C" {
 
 #define OR_NNODE 289          /* 1 keV .. 1 TeV, 32 bins per decade */
 #define OR_MAX_MAT 8
+#define OR_MAX_ELEM 8         /* elements of a compound */
 #define OR_MAX_VOL 512
 
 /* process bits for the single-interaction tests (0 = all enabled) */
@@ -56,12 +57,15 @@ float or_u01_f32(uint32_t w);
 uint64_t or_child_id(uint32_t seed, uint32_t event, uint64_t parent_id, uint32_t parent_step, uint32_t k);
 
 /* ---- setup: materials, geometry, cuts, tables ---- */
-/* mat_* arrays have n_mat entries; Z = 0 marks vacuum.
+/* mat_* arrays have n_mat entries; Z = 0 (and no elements) marks vacuum. A compound is given
+ * by mat_n_elem[m] > 0 elements, taken in order from elem_Z / elem_A / elem_atoms (atoms per
+ * formula unit); its own mat_Z and mat_A are then ignored. mat_n_elem = NULL: all elements. 
  * geometry: kind 0 = slab stack along z starting at z = 0, |x|,|y| <= half_xy;
  *           kind 1 = concentric tubes around z, |z| <= half_z, layer_r[n_layers] inner radii.
  * sub_mat/sub_thick: the sublayers of one layer (same for every layer). */
 or_ctx* or_create(int n_mat, const int* mat_Z, const double* mat_A, const double* mat_rho,
-                  const double* mat_I_eV, int kind, int n_layers, int n_sub, const int* sub_mat,
+                  const double* mat_I_eV, const int* mat_n_elem, const int* elem_Z, const double* elem_A,
+                  const double* elem_atoms, int kind, int n_layers, int n_sub, const int* sub_mat,
                   const double* sub_thick, double half_xy, double half_z, const double* layer_r,
                   double range_cut_mm, double field_T, double tracking_cut_MeV);
 void or_destroy(or_ctx* c);

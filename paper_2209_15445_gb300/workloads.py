@@ -39,6 +39,8 @@ class Material:
     A: float  # g/mol
     density: float  # g/cm^3
     I_eV: float  # mean excitation energy
+    # a compound: ((Z, A g/mol, atoms per formula unit), ...); Z and A above are then unused
+    elements: tuple = ()
 
 
 # PDG "Atomic and nuclear properties of materials" values
@@ -46,6 +48,8 @@ PB = Material("Pb", 82, 207.2, 11.35, 823.0)
 LAR = Material("lAr", 18, 39.948, 1.396, 188.0)
 SI = Material("Si", 14, 28.0855, 2.329, 173.0)
 FE = Material("Fe", 26, 55.845, 7.874, 286.0)
+# lead tungstate, the paper's compound (PDG: density 8.30 g/cm^3, I = 600.7 eV)
+PBWO4 = Material("PbWO4", 0, 0.0, 8.30, 600.7, elements=((82, 207.2, 1.0), (74, 183.84, 1.0), (8, 15.999, 4.0)))
 
 
 @dataclass
@@ -70,6 +74,12 @@ class Geometry:
 
 def slab_calorimeter(n_layers: int = 50) -> Geometry:
     return Geometry(kind=0, n_layers=n_layers, materials=[PB, LAR], sub_materials=[0, 1],
+                    sub_thickness=[2.3, 5.7], half_xy=200.0)
+
+
+def pbwo4_calorimeter(n_layers: int = 50) -> Geometry:
+    """the paper's validation calorimeter (Sec. 2.2): 50 layers of PbWO4 2.3 mm + lAr 5.7 mm"""
+    return Geometry(kind=0, n_layers=n_layers, materials=[PBWO4, LAR], sub_materials=[0, 1],
                     sub_thickness=[2.3, 5.7], half_xy=200.0)
 
 
