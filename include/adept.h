@@ -98,6 +98,16 @@ typedef struct {
   double A_g_mol;
   double density_g_cm3;
   double I_eV;
+  /* A compound (n_elements 1..8): its elements' Z, molar mass (g/mol) and atoms per formula
+   * unit, caller-owned and read only by adept_init; Z and A_g_mol are then ignored. The
+   * per-electron processes use the compound's electron density, photoabsorption sums over
+   * its atoms, 1/X0 adds its elements' terms by atom density (Bragg additivity), and the
+   * density effect takes its I and rho <Z/A>. n_elements = 0: a single element Z (Z = 0:
+   * vacuum). */
+  int32_t n_elements;
+  const int32_t* element_Z;
+  const double* element_A;
+  const double* element_atoms;
 } adept_material;
 
 /* Production cut as a range (converted to energy thresholds per material), uniform
@@ -333,8 +343,9 @@ int adept_raytrace(adept_ctx* ctx, int32_t prec, const double cam[11], int32_t n
  * device current; make that first call before any stream capture. Work is queued on stream
  * (a cudaStream_t; results are ready when the stream reaches it). Every call shares the
  * array, so calls that overlap on the GPU (other streams, other threads) race; serialise
- * them. Returns ADEPT_EINVAL for a null pointer, a bad material, a non-positive cut or
- * n_materials outside 1..ADEPT_NOALLOC_MAX_MATERIALS, ADEPT_ECUDA if the launch fails. */
+ * them. Returns ADEPT_EINVAL for a null pointer, a bad material or a compound (single
+ * elements only), a non-positive cut or n_materials outside 1..ADEPT_NOALLOC_MAX_MATERIALS,
+ * ADEPT_ECUDA if the launch fails. */
 #define ADEPT_NOALLOC_MAX_MATERIALS 4
 int adept_build_tables_noalloc(const adept_material* materials, int32_t n_materials, double range_cut_mm,
                                double* dev_tables, double* dev_cuts, void* stream);

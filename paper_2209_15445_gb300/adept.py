@@ -46,7 +46,22 @@ class adept_geometry(C.Structure):
 
 
 class adept_material(C.Structure):
-    _fields_ = [("Z", C.c_int32), ("A_g_mol", C.c_double), ("density_g_cm3", C.c_double), ("I_eV", C.c_double)]
+    _fields_ = [("Z", C.c_int32), ("A_g_mol", C.c_double), ("density_g_cm3", C.c_double), ("I_eV", C.c_double),
+                ("n_elements", C.c_int32), ("element_Z", C.POINTER(C.c_int32)),
+                ("element_A", C.POINTER(C.c_double)), ("element_atoms", C.POINTER(C.c_double))]
+
+
+def material_struct(m, keep):
+    """adept_material of a workloads.Material; the element arrays of a compound go to keep"""
+    els = getattr(m, "elements", ())
+    if not els:
+        return adept_material(m.Z, m.A, m.density, m.I_eV, 0, None, None, None)
+    z = np.array([e[0] for e in els], np.int32)
+    a = np.array([e[1] for e in els], np.float64)
+    n = np.array([e[2] for e in els], np.float64)
+    keep += [z, a, n]
+    return adept_material(0, 0.0, m.density, m.I_eV, len(els), z.ctypes.data_as(C.POINTER(C.c_int32)), _dp(a),
+                          _dp(n))
 
 
 class adept_cuts(C.Structure):
@@ -274,7 +289,8 @@ def adept_probe_distance(h, prec, pos, d, vol, T, q):
 
 def adept_build_tables_noalloc(materials, range_cut_mm, dev_tables_ptr, dev_cuts_ptr, stream):
     """Forward to the allocation-free table build; materials is a list of workloads.Material."""
-    arr = (adept_material * len(materials))(*[adept_material(m.Z, m.A, m.density, m.I_eV) for m in materials])
+    keep = []
+    arr = (adept_material * len(materials))(*[material_struct(m, keep) for m in materials])
     return load().adept_build_tables_noalloc(arr, len(materials), range_cut_mm, dev_tables_ptr, dev_cuts_ptr, stream)
 
 
@@ -345,8 +361,7 @@ class Transport:
         self.stream = torch.cuda.Stream()
         self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device="cuda")
         self._keep = []
-        mats = (adept_material * len(geom.materials))(
-            *[adept_material(m.Z, m.A, m.density, m.I_eV) for m in geom.materials])
+        mats = (adept_material * len(geom.materials))(*[material_struct(m, self._keep) for m in geom.materials])
         lm = np.array(geom.sub_materials, np.int32)
         th = np.array(geom.sub_thickness, np.float64)
         lr = np.array(geom.layer_r if geom.layer_r else [0.0], np.float64)

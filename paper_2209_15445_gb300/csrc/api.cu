@@ -97,6 +97,7 @@ struct adept_ctx {
   Params P{};
   MatDev* mat_dev = nullptr;
   double* mat_in = nullptr;
+  std::vector<double> mat_rec;  // kMatRec doubles per material (elements of compounds copied)
   BuildScratch scratch{};
   double2 *g64 = nullptr, *e64 = nullptr, *p64 = nullptr;
   float2 *g32 = nullptr, *e32 = nullptr, *p32 = nullptr;
@@ -178,6 +179,9 @@ static bool carve_n(adept_ctx* c, T** out, size_t n) {
   return *out != nullptr;
 }
 
+// an element with Z > 0 or a compound (Z = 0 and no elements: vacuum)
+static bool is_matter(const adept_material& m) { return m.Z > 0 || m.n_elements > 0; }
+
 // volumes of the calorimeter: slab planes, or tube radii with vacuum inside and between
 static int build_geometry(adept_ctx* c, const adept_geometry* g) {
   if (g->kind != 0 && g->kind != 1) return fail(c, ADEPT_EINVAL, "geometry kind must be 0 or 1");
@@ -193,7 +197,7 @@ static int build_geometry(adept_ctx* c, const adept_geometry* g) {
   c->kind = g->kind;
   c->n_bins = g->n_layers * g->n_mat_per_layer;
   c->bnd.clear(); c->vol_mat.clear(); c->vol_bin.clear();
-  auto mat_of = [&](int s) { return c->mats[g->layer_materials[s]].Z > 0 ? g->layer_materials[s] : -1; };
+  auto mat_of = [&](int s) { return is_matter(c->mats[g->layer_materials[s]]) ? g->layer_materials[s] : -1; };
   if (g->kind == 0) {
     if (!(g->transverse_half_mm > 0.0)) return fail(c, ADEPT_EINVAL, "transverse_half_mm must be > 0");
     double z = 0.0;
@@ -260,8 +264,28 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (reinterpret_cast<uintptr_t>(dev_arena) & 255) return ADEPT_EINVAL;
   c->n_mat = n_materials;
   c->mats.assign(materials, materials + n_materials);
-  for (auto& m : c->mats)
-    if (m.Z < 0 || m.Z > 100 || (m.Z > 0 && !(m.A_g_mol > 0 && m.density_g_cm3 > 0 && m.I_eV > 0))) return ADEPT_EINVAL;
+  c->mat_rec.assign((size_t)kMatRec * kMaxMat, 0.0);
+  for (int k = 0; k < n_materials; ++k) {
+    adept_material& m = c->mats[k];
+    double* r = c->mat_rec.data() + (size_t)kMatRec * k;
+    if (m.n_elements < 0 || m.n_elements > kMaxElem) return ADEPT_EINVAL;
+    if (m.n_elements > 0) {  // a compound: keep its elements (the caller's arrays are borrowed)
+      if (!m.element_Z || !m.element_A || !m.element_atoms || !(m.density_g_cm3 > 0 && m.I_eV > 0))
+        return ADEPT_EINVAL;
+      for (int i = 0; i < m.n_elements; ++i) {
+        if (m.element_Z[i] < 1 || m.element_Z[i] > 100 || !(m.element_A[i] > 0) || !(m.element_atoms[i] > 0))
+          return ADEPT_EINVAL;
+        r[5 + 3 * i] = m.element_Z[i];
+        r[5 + 3 * i + 1] = m.element_A[i];
+        r[5 + 3 * i + 2] = m.element_atoms[i];
+      }
+    } else if (m.Z < 0 || m.Z > 100 || (m.Z > 0 && !(m.A_g_mol > 0 && m.density_g_cm3 > 0 && m.I_eV > 0))) {
+      return ADEPT_EINVAL;
+    }
+    r[0] = m.n_elements > 0 ? 0.0 : m.Z;
+    r[1] = m.A_g_mol; r[2] = m.density_g_cm3; r[3] = m.I_eV; r[4] = m.n_elements;
+    m.element_Z = nullptr; m.element_A = nullptr; m.element_atoms = nullptr;
+  }
   if (!(cuts->range_cut_mm > 0.0) || !(cuts->tracking_cut_MeV >= 1e-3) || !(cuts->tracking_cut_MeV < 1e4))
     return ADEPT_EINVAL;
   if (options) c->opt = *options;
@@ -304,7 +328,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   bool ok = carve_n(cp, &P.ctrl, 1);
   double* bnd = nullptr; int *vm = nullptr, *vb = nullptr;
   ok = ok && carve_n(cp, &bnd, c->bnd.size()) && carve_n(cp, &vm, c->n_vol) && carve_n(cp, &vb, c->n_vol);
-  ok = ok && carve_n(cp, &c->mat_dev, kMaxMat) && carve_n(cp, &c->mat_in, 4 * kMaxMat);
+  ok = ok && carve_n(cp, &c->mat_dev, kMaxMat) && carve_n(cp, &c->mat_in, kMatRec * kMaxMat);
   const size_t nn = (size_t)kNNode * n_materials;
   ok = ok && carve_n(cp, &c->scratch.vals, 14 * nn) && carve_n(cp, &c->scratch.bins, 3 * nn);
   ok = ok && carve_n(cp, &c->g64, nn * kNTabG) && carve_n(cp, &c->e64, nn * kNTabE) && carve_n(cp, &c->p64, nn * kNTabP);
@@ -424,11 +448,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
 
 extern "C" int adept_build_tables(adept_ctx* c) {
   if (!c) return ADEPT_EINVAL;
-  std::vector<double> in(4 * kMaxMat, 0.0);
-  for (int m = 0; m < c->n_mat; ++m) {
-    in[4 * m] = c->mats[m].Z; in[4 * m + 1] = c->mats[m].A_g_mol;
-    in[4 * m + 2] = c->mats[m].density_g_cm3; in[4 * m + 3] = c->mats[m].I_eV;
-  }
+  const std::vector<double>& in = c->mat_rec;
   CK(cudaMemcpyAsync(c->mat_in, in.data(), sizeof(double) * in.size(), cudaMemcpyHostToDevice, c->stream));
   CK(launch_build_tables(c->P, c->mat_in, c->n_mat, c->range_cut, c->mat_dev, c->scratch, c->g64, c->e64, c->p64,
                          c->g32, c->e32, c->p32, c->re64, c->rp64, c->re32, c->rp32, c->Tc, c->kc, c->stream));
@@ -1185,7 +1205,7 @@ extern "C" int adept_probe_continuous(adept_ctx* c, int32_t which, int32_t speci
   if (!c || which < 0 || which > 1 || (species != 1 && species != 2) || m < 0 || m >= c->n_mat ||
       (prec != 0 && prec != 1) || (n && !host_out) || !(T >= 1e-3 && T <= 1e6) || !(s >= 0.0))
     return ADEPT_EINVAL;
-  if (c->mats[m].Z <= 0) return fail(c, ADEPT_EINVAL, "material %d is vacuum", m);
+  if (!is_matter(c->mats[m])) return fail(c, ADEPT_EINVAL, "material %d is vacuum", m);
   if (!c->built) return fail(c, ADEPT_ESTATE, "tables not built");
   const size_t per = which == 0 ? 24 : 16;
   if (n > c->probe_bytes / per) return fail(c, ADEPT_EINVAL, "at most %zu draws per call", c->probe_bytes / per);

@@ -18,7 +18,7 @@ __device__ inline double node_E(int i) { return exp(kLnEmin + (double)i * kDlog)
 
 __global__ void k_materials(const double* in, int n, MatDev* out) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m < n) init::setup_material(in + 4 * m, out + m);
+  if (m < n) init::setup_material(in + kMatRec * m, out + m);
 }
 
 __device__ inline double s_full(const MatDev& M, double T) {

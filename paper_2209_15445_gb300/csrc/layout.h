@@ -26,8 +26,14 @@ struct GeoView {
 };
 
 // per-material constants derived on the device from (Z, A, rho, I)
+constexpr int kMaxElem = 8;                    // elements of a compound
+constexpr int kMatRec = 5 + 3 * kMaxElem;      // material record: Z, A, rho, I, n_elem, (Z, A, atoms) x n_elem
+
 struct MatDev {
-  double Z, A, rho, I;   // I in eV
+  double Z, A, rho, I;   // I in eV (a compound: its mean Z and A)
+  int n_elem;            // elements: Z and atoms per mm^3
+  double eZ[kMaxElem], en_at[kMaxElem];
+  double ZoA;            // <Z/A> by mass
   double n_at, n_el;     // per mm^3
   double inv_x0;         // 1/mm
   double cbar, x0, x1, a_d;

@@ -24,7 +24,7 @@ constexpr int kNoAllocMat = ADEPT_NOALLOC_MAX_MATERIALS;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMat * kRows * kNNode];
 
 struct MatIn {
-  double v[kNoAllocMat][4];  // Z, A, rho, I per material, passed by value
+  double v[kNoAllocMat][kMatRec];  // material records (elements only), passed by value
 };
 
 enum { R_MUC, R_MUP, R_MUPH, R_SFULL, R_SE, R_IE, R_BE, R_SP, R_IP, R_BP, R_AP, R_RFULL, R_RE, R_RP, R_BFULL, R_BE_, R_BP_ };
@@ -150,8 +150,9 @@ extern "C" int adept_build_tables_noalloc(const adept_material* materials, int32
   MatIn in{};
   for (int m = 0; m < n_materials; ++m) {
     const adept_material& t = materials[m];
+    if (t.n_elements != 0) return ADEPT_EINVAL;  // single elements only
     if (t.Z < 0 || t.Z > 100 || (t.Z > 0 && !(t.A_g_mol > 0 && t.density_g_cm3 > 0 && t.I_eV > 0))) return ADEPT_EINVAL;
-    in.v[m][0] = t.Z; in.v[m][1] = t.A_g_mol; in.v[m][2] = t.density_g_cm3; in.v[m][3] = t.I_eV;
+    in.v[m][0] = t.Z; in.v[m][1] = t.A_g_mol; in.v[m][2] = t.density_g_cm3; in.v[m][3] = t.I_eV; in.v[m][4] = 0.0;
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return ADEPT_ECUDA;

@@ -28,21 +28,57 @@ __device__ inline double sigma_kn(double k) {
   return 2.0 * kPi * kRe * kRe * s;
 }
 
+// Tsai radiation length per atom (PDG): Lrad = ln(184.15 Z^-1/3), L'rad = ln(1194 Z^-2/3),
+// Coulomb correction f(Z) of Davies, Bethe and Maximon; 1/X0 = n_at x this
+__device__ inline double inv_x0_per_atom(double Z) {
+  const double lz = log(Z);
+  const double a2 = (kAlpha * Z) * (kAlpha * Z);
+  const double f = a2 * (1.0 / (1.0 + a2) + 0.20206 - 0.0369 * a2 + 0.0083 * a2 * a2 - 0.002 * a2 * a2 * a2);
+  return 4.0 * kAlpha * kRe * kRe * (Z * Z * ((log(184.15) - lz / 3.0) - f) + Z * (log(1194.0) - 2.0 * lz / 3.0));
+}
+
+// in: a kMatRec material record. An element (n_elem = 0) is one atom kind; a compound
+// lists its elements with their atoms per formula unit, and its atom densities follow from
+// the formula's mass fractions.
 __device__ inline void setup_material(const double* in, MatDev* m) {
   m->Z = in[0]; m->A = in[1]; m->rho = in[2]; m->I = in[3];
-  m->vacuum = !(m->Z > 0.0);
+  const int ne = (int)in[4];
+  m->vacuum = !(m->Z > 0.0) && ne == 0;
+  m->n_elem = 0;
   if (m->vacuum) return;
-  m->n_at = kNA * m->rho / m->A * 1e-3;
-  m->n_el = m->Z * m->n_at;
-  // Tsai radiation length (PDG): Lrad = ln(184.15 Z^-1/3), L'rad = ln(1194 Z^-2/3),
-  // Coulomb correction f(Z) of Davies, Bethe and Maximon
-  const double lz = log(m->Z);
-  const double a2 = (kAlpha * m->Z) * (kAlpha * m->Z);
-  const double f = a2 * (1.0 / (1.0 + a2) + 0.20206 - 0.0369 * a2 + 0.0083 * a2 * a2 - 0.002 * a2 * a2 * a2);
-  m->inv_x0 = 4.0 * kAlpha * kRe * kRe * m->n_at *
-              (m->Z * m->Z * ((log(184.15) - lz / 3.0) - f) + m->Z * (log(1194.0) - 2.0 * lz / 3.0));
+  if (ne > 0) {
+    double M = 0.0, natoms = 0.0, zsum = 0.0;
+    for (int i = 0; i < ne; ++i) {
+      M += in[5 + 3 * i + 2] * in[5 + 3 * i + 1];
+      natoms += in[5 + 3 * i + 2];
+      zsum += in[5 + 3 * i + 2] * in[5 + 3 * i];
+    }
+    m->n_elem = ne;
+    m->ZoA = 0.0; m->n_at = 0.0; m->n_el = 0.0;
+    for (int i = 0; i < ne; ++i) {
+      const double Zi = in[5 + 3 * i], Ai = in[5 + 3 * i + 1];
+      const double w = in[5 + 3 * i + 2] * Ai / M;
+      m->eZ[i] = Zi;
+      m->en_at[i] = kNA * m->rho * w / Ai * 1e-3;
+      m->ZoA += w * Zi / Ai;
+      m->n_at += m->en_at[i];
+      m->n_el += Zi * m->en_at[i];
+    }
+    m->A = M / natoms;
+    m->Z = zsum / natoms;
+  } else {
+    m->n_at = kNA * m->rho / m->A * 1e-3;
+    m->n_el = m->Z * m->n_at;
+    m->n_elem = 1;
+    m->eZ[0] = m->Z;
+    m->en_at[0] = m->n_at;
+    m->ZoA = m->Z / m->A;
+  }
+  // a compound adds its elements' terms by atom density (Bragg additivity of 1/X0)
+  m->inv_x0 = 0.0;
+  for (int i = 0; i < m->n_elem; ++i) m->inv_x0 += m->en_at[i] * inv_x0_per_atom(m->eZ[i]);
   // Sternheimer-Peierls general density-effect parameters for condensed media
-  const double hwp = 28.816 * sqrt(m->rho * m->Z / m->A);
+  const double hwp = 28.816 * sqrt(m->rho * m->ZoA);
   m->cbar = 2.0 * log(m->I / hwp) + 1.0;
   if (m->I < 100.0) {
     m->x1 = 2.0;
@@ -66,12 +102,17 @@ __device__ inline double mu_pair(const MatDev& m, double E) {
 }
 
 // Born-approximation K-shell photoabsorption: 4 sqrt(2) alpha^4 Z^5 sigma_Th (m/E)^3.5
+// (a compound: the sum over its atoms)
 __device__ inline double mu_photo(const MatDev& m, double E) {
   const double q = kMe / E;
   const double a2 = kAlpha * kAlpha;
-  const double z2 = m.Z * m.Z;
-  return m.n_at * 4.0 * sqrt(2.0) * (a2 * a2) * (z2 * z2 * m.Z) * (8.0 * kPi / 3.0 * kRe * kRe) *
+  double s = 0.0;
+  for (int i = 0; i < m.n_elem; ++i) {
+    const double Z = m.eZ[i], z2 = Z * Z;
+    s += m.en_at[i] * 4.0 * sqrt(2.0) * (a2 * a2) * (z2 * z2 * Z) * (8.0 * kPi / 3.0 * kRe * kRe) *
          (q * q * q * sqrt(q));
+  }
+  return s;
 }
 
 __device__ inline double density_delta(const MatDev& m, double T) {
