@@ -70,7 +70,7 @@ def args_parse():
     ap.add_argument("--arena-gb", type=float, default=10.0)
     ap.add_argument("--bps", type=int, default=0, help="transport-kernel blocks/SM variant (0 = library default)")
     ap.add_argument("--bps-species", type=str, default="", help="per-species variants gamma,e-,e+")
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "rt"],
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "rt", "batch"],
                     help="c2 (default) is the headline line; the others are the configuration studies")
     ap.add_argument("--seconds", type=float, default=20.0, help="serving workload duration")
     ap.add_argument("--genlog", default="", help="write the per-generation queue sizes of the last step here")
@@ -417,6 +417,28 @@ def run_study(a):
                 "cpu_baseline": {"value": cpu, "unit": "pixels/s", "cores": 1, "kind": "oracle",
                                  "sample": "256 x 256 image of the same view, FP64 C oracle, one thread"}}
         print(json.dumps(line))
+        return
+    if a.workload == "batch":
+        # throughput against the number of 10 GeV e- showers transported together (paper
+        # Sec. 5: batching primaries keeps the GPU busy); one line per batch size
+        geom = W.slab_calorimeter()
+        tr = A.Transport(geom, precision=1, arena_bytes=int(a.arena_gb * (1 << 30)), max_events=65536)
+        rows = []
+        for nb in (1, 10, 100, 1000, 10000, 30000):
+            arr = A.tracks_array(W.electrons(nb, 1e4))
+            rid = tr.submit(arr); tr.transport(); tr.result(rid, nb)
+            s0 = tr.stats(); torch.cuda.synchronize(); t0 = time.perf_counter()
+            reps = max(1, min(a.steps, int(30000 / nb)))
+            for _ in range(reps):
+                rid = tr.submit(arr); tr.transport(); tr.result(rid, nb)
+            torch.cuda.synchronize(); dt = time.perf_counter() - t0; s1 = tr.stats()
+            st = sum(s1.steps) - sum(s0.steps)
+            rows.append({"showers_per_batch": nb, "steps_per_s": st / dt, "showers_per_s": nb * reps / dt,
+                         "ms_per_batch": 1e3 * dt / reps})
+        tr.close()
+        print(json.dumps(_line(a, "10 GeV e- showers in batches of 1 to 30,000 (slab, split, end to end through the "
+                                  "C ABI with host buffers)", rows[-2]["steps_per_s"], rows[-2]["ms_per_batch"] / 1e3,
+                               {"batches": rows})))
         return
     if a.workload == "c1":
         # plain FP64, one event per transport, one generation per launch with the queue
