@@ -297,7 +297,8 @@ def run_ours(a):
     peak, peak_kind = peaks()
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else None
     traffic = None
-    if NCU_BYTES_PER_STEP and NCU_SRC_HASH == kernel_src_hash() and kern_n:
+    # the ncu figure was taken on the split form's kernels; other forms report none
+    if NCU_BYTES_PER_STEP and a.precision == 1 and NCU_SRC_HASH == kernel_src_hash() and kern_n:
         traffic = NCU_BYTES_PER_STEP * steps / kern_n
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
