@@ -154,7 +154,7 @@ typedef struct {
   double delta_intersection_mm; /* [0.001] */
   uint32_t max_outgoing;      /* outgoing particles kept between two status reads (a ring in the
                                  arena, 64 bytes each); more make adept_transport return
-                                 ADEPT_ENOMEM [1048576] */
+                                 ADEPT_ENOMEM [arena_bytes / 1024, within 2^16 .. 2^26] */
 } adept_options;
 
 /* adept_options.flags: time every generation (its three transport kernels, from the fork to

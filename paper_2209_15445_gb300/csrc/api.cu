@@ -315,7 +315,8 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (o.max_events == 0) o.max_events = 65536;
   if (o.max_generation_log == 0) o.max_generation_log = 4096;
   if (o.max_generation_log > (uint32_t)kMaxLogGen) o.max_generation_log = kMaxLogGen;
-  if (o.max_outgoing == 0) o.max_outgoing = 1u << 20;
+  if (o.max_outgoing == 0)  // a sixteenth of the arena (64 bytes a record), 2^16 .. 2^26 records
+    o.max_outgoing = (uint32_t)std::min<size_t>(std::max<size_t>(arena_bytes / 1024, (size_t)1 << 16), (size_t)1 << 26);
   if (!(o.tracks_per_MeV > 0.0)) o.tracks_per_MeV = 0.25;
   c->range_cut = cuts->range_cut_mm;
   int rc = build_geometry(c.get(), geometry);
