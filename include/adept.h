@@ -18,8 +18,9 @@
  *    library from adept_init until adept_destroy.
  *  - stream is a cudaStream_t passed as void* (e.g. torch.cuda.Stream.cuda_stream);
  *    all device work of the context is ordered on it.
- *  - Threading: adept_submit, adept_poll and adept_get_scoring are thread-safe;
- *    adept_transport must be called from one thread at a time per context.
+ *  - Threading: adept_submit, adept_submit_device, adept_poll, adept_wait,
+ *    adept_get_leaked and adept_get_scoring are thread-safe; adept_transport must be
+ *    called from one thread at a time per context.
  */
 #ifndef ADEPT_H
 #define ADEPT_H
@@ -34,7 +35,8 @@ extern "C" {
 /* ---- status codes ---- */
 #define ADEPT_OK 0
 #define ADEPT_EINVAL (-1)   /* invalid argument (null pointer, bad size, bad geometry) */
-#define ADEPT_ENOMEM (-2)   /* arena too small, or track capacity exceeded during transport */
+#define ADEPT_ENOMEM (-2)   /* arena too small, or the track queues or the outgoing-particle
+                                ring overflowed during transport */
 #define ADEPT_ESTATE (-3)   /* call out of order (e.g. transport before adept_build_tables) */
 #define ADEPT_ECUDA (-4)    /* a CUDA runtime call failed; see adept_last_error */
 #define ADEPT_ETIMEOUT (-5) /* adept_transport hit its time budget with work left */
@@ -233,7 +235,10 @@ int adept_build_tables(adept_ctx* ctx);
 int adept_submit(adept_ctx* ctx, const adept_track* host_tracks, size_t n, uint32_t* request_id);
 
 /* Same, but the tracks are already in device memory (n records laid out as
- * adept_track) -- used to time transport with inputs resident in HBM. */
+ * adept_track) -- used to time transport with inputs resident in HBM. The records must be
+ * written when the call is made (the library reads their event, pdg and energy fields on
+ * a stream of its own) and must stay in place until the request has been admitted, which
+ * happens at the start of a later adept_transport. Thread-safe. */
 int adept_submit_device(adept_ctx* ctx, const void* dev_tracks, size_t n, uint32_t* request_id);
 
 /* Run the stepping loop until every submitted request (including requests submitted
@@ -350,6 +355,8 @@ int adept_raytrace(adept_ctx* ctx, int32_t prec, const double cam[11], int32_t n
 int adept_build_tables_noalloc(const adept_material* materials, int32_t n_materials, double range_cut_mm,
                                double* dev_tables, double* dev_cuts, void* stream);
 
+/* Message of the last failure on this context, from any thread. The pointer stays valid
+ * until the next failure or adept_destroy. */
 const char* adept_last_error(const adept_ctx* ctx);
 void adept_destroy(adept_ctx* ctx);
 

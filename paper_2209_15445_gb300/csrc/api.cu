@@ -81,6 +81,8 @@ struct SlotAlloc {  // first-fit allocator of contiguous event-slot ranges
 }  // namespace
 
 struct adept_ctx {
+  std::mutex err_mu;  // producers and the transport thread may both fail
+  std::mutex submit_mu;  // device submissions share submit_stream
   std::string err;
   cudaStream_t stream = nullptr;
   adept_options opt{};
@@ -119,6 +121,7 @@ struct adept_ctx {
   cudaEvent_t status_ev[2] = {nullptr, nullptr};
   cudaEvent_t stage_ev = nullptr;            // the last copy out of the pinned staging buffer
   cudaStream_t copy_stream = nullptr;        // result copies, overlapping the next chunk
+  cudaStream_t submit_stream = nullptr;      // device submissions' field reads (producer threads)
   char* h_stage = nullptr;
   size_t h_stage_bytes = 0;
   // launch shape
@@ -155,6 +158,7 @@ static int fail(adept_ctx* c, int code, const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
+    std::lock_guard<std::mutex> lk(c->err_mu);
     c->err = buf;
   }
   return code;
@@ -413,6 +417,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     }
     CK(cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
     CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->submit_stream, cudaStreamNonBlocking));
     for (int j = 0; j < 2; ++j) {
       CK(cudaStreamCreateWithFlags(&c->side[j], cudaStreamNonBlocking));
       CK(cudaEventCreateWithFlags(&c->join[j], cudaEventDisableTiming));
@@ -540,13 +545,16 @@ extern "C" int adept_submit_device(adept_ctx* c, const void* dev_tracks, size_t 
   if (n) {
     // read back the three fields the host needs for numbering and admission
     const char* base = static_cast<const char*>(dev_tracks);
+    // (on a stream of its own: a producer must not wait for the transport's queued work)
+    cudaStream_t ss = c->submit_stream;
+    std::lock_guard<std::mutex> lk(c->submit_mu);
     CK(cudaMemcpy2DAsync(ev.data(), 4, base + offsetof(adept_track, event), sizeof(adept_track), 4, n,
-                         cudaMemcpyDeviceToHost, c->stream));
+                         cudaMemcpyDeviceToHost, ss));
     CK(cudaMemcpy2DAsync(pdg.data(), 4, base + offsetof(adept_track, pdg), sizeof(adept_track), 4, n,
-                         cudaMemcpyDeviceToHost, c->stream));
+                         cudaMemcpyDeviceToHost, ss));
     CK(cudaMemcpy2DAsync(E.data(), 8, base + offsetof(adept_track, E_kin_MeV), sizeof(adept_track), 8, n,
-                         cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+                         cudaMemcpyDeviceToHost, ss));
+    CK(cudaStreamSynchronize(ss));
   }
   int rc = prepare_request(
       c, *r, [&](size_t i) { return ev[i]; }, [&](size_t i) { return pdg[i]; }, [&](size_t i) { return E[i]; });
@@ -1217,7 +1225,11 @@ extern "C" int adept_probe_continuous(adept_ctx* c, int32_t which, int32_t speci
   return ADEPT_OK;
 }
 
-extern "C" const char* adept_last_error(const adept_ctx* c) { return c ? c->err.c_str() : "null context"; }
+extern "C" const char* adept_last_error(const adept_ctx* c) {
+  if (!c) return "null context";
+  std::lock_guard<std::mutex> lk(const_cast<adept_ctx*>(c)->err_mu);
+  return c->err.c_str();
+}
 
 extern "C" void adept_destroy(adept_ctx* c) {
   if (!c) return;
@@ -1229,6 +1241,7 @@ extern "C" void adept_destroy(adept_ctx* c) {
     if (c->side[j]) { cudaStreamSynchronize(c->side[j]); cudaStreamDestroy(c->side[j]); }
     if (c->join[j]) cudaEventDestroy(c->join[j]);
   }
+  if (c->submit_stream) { cudaStreamSynchronize(c->submit_stream); cudaStreamDestroy(c->submit_stream); }
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->tstream) { cudaStreamSynchronize(c->tstream); cudaStreamDestroy(c->tstream); }
   for (int j = 0; j < 3; ++j)
