@@ -638,9 +638,10 @@ static bool timing_species(const adept_ctx* c) { return (c->opt.flags & ADEPT_FL
 // Timing events are recorded on tstream: the start one after the generation's fork, an end
 // one after each kernel it times. tstream joins the chain only at the end of the chunk, so
 // the records never delay the next generation.
-static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b) {
+static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b, bool captured) {
   cudaError_t e = cudaMemsetAsync(&c->P.ctrl->done_count[b], 0, sizeof(uint32_t), c->stream);
-  const unsigned rf = cudaEventRecordExternal;
+  // inside a capture a timing record must be an external event node; outside, a plain record
+  const unsigned rf = captured ? cudaEventRecordExternal : cudaEventRecordDefault;
   const bool T = timing(c), TS = timing_species(c);
   cudaEvent_t* ev = c->ev.empty() ? nullptr : c->ev.data() + 4 * gens * b;
   cudaStream_t ts = c->tstream;
@@ -687,7 +688,7 @@ static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b) {
 static int capture_graph(adept_ctx* c, int gens, int b) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = enqueue_generations(c, gens, b);
+  cudaError_t e = enqueue_generations(c, gens, b, true);
   cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
   if (e != cudaSuccess) return fail(c, ADEPT_ECUDA, "graph capture: %s", cudaGetErrorString(e));
   if (e2 != cudaSuccess) return fail(c, ADEPT_ECUDA, "graph capture end: %s", cudaGetErrorString(e2));
@@ -717,7 +718,7 @@ static int launch_chunk(adept_ctx* c, int b) {
     }
     CK(cudaGraphLaunch(c->graph[b], c->stream));
   } else {
-    CK(enqueue_generations(c, 1, b));
+    CK(enqueue_generations(c, 1, b, false));
   }
   c->stats.launches += (c->opt.fused ? 1 : 4) * gens + 2;
   CK(cudaMemcpyAsync(c->h_ctrl[b], c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));

@@ -264,3 +264,21 @@ def test_secondary_counts_and_step_lengths(precision):
             keep = (a + b) > 50
             chi2 = np.sum((a[keep] - b[keep]) ** 2 / (a[keep] + b[keep]))
             assert stats.chi2.sf(chi2, keep.sum()) > 1e-4, (sp, chi2, keep.sum())
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_one_generation_per_launch_without_graphs(fused):
+    """the small-batch form: no CUDA graphs, one generation per launch and the queue sizes
+    read back after each; the same per-generation queues as the oracle, with the timing
+    events on"""
+    need_gpu()
+    from paper_2209_15445_gb300 import adept as A
+    geom = W.slab_calorimeter()
+    flags = A.FLAG_TIME_STEPS if fused else A.FLAG_TIME_SPECIES
+    tr = make(geom, precision=0, graph_generations=-1, fused=fused, flags=flags, tuned=False)
+    prim = W.mixed(4, seed=22)
+    prim.E[:] = np.minimum(prim.E, 1000.0)
+    compare_generations(tr, oracle.Oracle(geom), prim, 0)
+    st = tr.stats()
+    assert st.step_launches > 10 and st.step_kernel_ms > 0
+    tr.close()
