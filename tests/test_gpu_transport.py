@@ -282,3 +282,35 @@ def test_one_generation_per_launch_without_graphs(fused):
     st = tr.stats()
     assert st.step_launches > 10 and st.step_kernel_ms > 0
     tr.close()
+
+
+def test_admission_waits_for_slots_and_energy_budget():
+    """more requests than event slots, and an energy budget that admits a few at a time:
+    every request completes, each with the result it gets alone"""
+    need_gpu()
+    geom = W.slab_calorimeter()
+    reqs = [W.electrons(20, 300.0, first_event=1000 * k) for k in range(10)]
+    alone = []
+    tr = make(geom, precision=1, tuned=False)
+    for r in reqs:
+        alone.append(gpu_run(tr, r)[0])
+    tr.close()
+    # 64 slots hold three requests of 20 events; a queue capacity of 4096 at 0.3 tracks/MeV
+    # is an energy budget of 13.6 GeV, two of these 6 GeV requests at a time
+    tr = make(geom, precision=1, max_events=64, track_capacity=4096, tracks_per_MeV=0.3, tuned=False)
+    ids = [tr.submit(r) for r in reqs]
+    tr.transport()
+    for rid, a in zip(ids, alone):
+        got, meta = tr.result(rid, 20)
+        np.testing.assert_allclose(got, a, rtol=1e-9, atol=1e-9)
+    tr.close()
+
+
+def test_block_size_128_matches_oracle():
+    need_gpu()
+    geom = W.slab_calorimeter()
+    tr = make(geom, precision=0, block_size=128, graph_generations=16, tuned=False)
+    prim = W.mixed(5, seed=24)
+    prim.E[:] = np.minimum(prim.E, 1500.0)
+    compare_generations(tr, oracle.Oracle(geom), prim, 0)
+    tr.close()
