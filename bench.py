@@ -505,8 +505,8 @@ def run_study(a):
     # serving keeps few tracks per generation in flight: one fused kernel per generation
     # (less launch latency per generation) serves it faster than concurrent species kernels
     fo = {"fused": a.fused if a.fused >= 0 else 1}
-    tr = A.Transport(geom, precision=a.precision, field_T=3.8, arena_bytes=24 << 30, graph_generations=8,
-                     max_events=65536, tracks_per_MeV=0.1, **fo)
+    tr = A.Transport(geom, precision=a.precision, field_T=3.8, arena_bytes=24 << 30,
+                     graph_generations=a.graph or 8, max_events=65536, tracks_per_MeV=0.1, **fo)
     stop = threading.Event()
     lat, done_steps, errors = [], [0], []
     lock = threading.Lock()
