@@ -37,18 +37,12 @@ __global__ void __launch_bounds__(256, MINB) k_fused_generation(Params P) {
   const uint32_t n2 = min(__ldcg(&P.ctrl->count[p][2]), P.cap);
   const uint32_t T0 = (n0 + 31) >> 5, T1 = (n1 + 31) >> 5, T2 = (n2 + 31) >> 5;
   unsigned long long nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
-  uint32_t head = 0, tail = 0;
   uint32_t first = blockIdx.x * wpb + (threadIdx.x >> 5);
-  for (uint32_t t = first; t < T0; t += nwarps) run_tile<R, 0>(P, p, t << 5, n0, ring, head, tail, nsteps, ncreated);
-  if (tail != head) { drain<R, 0>(P, p, ring, head, tail - head, ncreated); head = tail; }
-  __syncwarp();
+  run_tiles<R, 0>(P, p, first, T0, nwarps, n0, ring, nsteps, ncreated);
   first = next_first(first, T0, nwarps);
-  for (uint32_t t = first; t < T1; t += nwarps) run_tile<R, 1>(P, p, t << 5, n1, ring, head, tail, nsteps, ncreated);
-  if (tail != head) { drain<R, 1>(P, p, ring, head, tail - head, ncreated); head = tail; }
-  __syncwarp();
+  run_tiles<R, 1>(P, p, first, T1, nwarps, n1, ring, nsteps, ncreated);
   first = next_first(first, T1, nwarps);
-  for (uint32_t t = first; t < T2; t += nwarps) run_tile<R, 2>(P, p, t << 5, n2, ring, head, tail, nsteps, ncreated);
-  if (tail != head) drain<R, 2>(P, p, ring, head, tail - head, ncreated);
+  run_tiles<R, 2>(P, p, first, T2, nwarps, n2, ring, nsteps, ncreated);
   if ((threadIdx.x & 31) == 0)
     for (int k = 0; k < 3; ++k) {
       if (nsteps[k]) atomicAdd(&s_cnt[k], nsteps[k]);

@@ -403,11 +403,10 @@ __device__ __forceinline__ void drain(const Params& P, int p, WarpRing<R>& ring,
 }
 
 // One warp takes 32 consecutive tracks of species S: phase A for each, appends the
-// survivors, queues the interactions and runs full warps of them as they accumulate.
+// survivors and queues the interactions.
 template <class R, int S, int V = 0>
 __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, uint32_t n, WarpRing<R>& ring,
-                                         uint32_t& head, uint32_t& tail, unsigned long long* nsteps,
-                                         unsigned long long* ncreated) {
+                                         uint32_t& tail, unsigned long long* nsteps, unsigned long long* ncreated) {
   const int lane = threadIdx.x & 31;
   const uint32_t i = base + lane;
   const bool active = i < n;
@@ -436,9 +435,29 @@ __device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, 
   }
   tail += __popc(need);
   __syncwarp();
-  while (tail - head >= 32u) {
-    drain<R, S>(P, p, ring, head, 32u, ncreated);
-    head += 32u;
+}
+
+// All of one warp's tiles of species S (tile, tile + stride, ... below tiles): phase A tile
+// by tile, a full warp of interactions whenever 32 wait, and the rest at the end. Phase A
+// and the interactions each have one call site, so the samplers are inlined once per kernel.
+template <class R, int S, int V = 0>
+__device__ __forceinline__ void run_tiles(const Params& P, int p, uint32_t tile, uint32_t tiles, uint32_t stride,
+                                          uint32_t n, WarpRing<R>& ring, unsigned long long* nsteps,
+                                          unsigned long long* ncreated) {
+  uint32_t head = 0, tail = 0;
+  for (;;) {
+    const uint32_t waiting = tail - head;
+    if (waiting < 32u) {
+      if (tile < tiles) {
+        run_tile<R, S, V>(P, p, tile << 5, n, ring, tail, nsteps, ncreated);
+        tile += stride;
+        continue;
+      }
+      if (waiting == 0u) break;
+    }
+    const uint32_t c = min(waiting, 32u);
+    drain<R, S>(P, p, ring, head, c, ncreated);
+    head += c;
     __syncwarp();
   }
 }
@@ -463,11 +482,8 @@ __global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
   const uint32_t tiles = (n + 31) >> 5;
   const uint32_t wpb = blockDim.x >> 5;
   WarpRing<R>& ring = rings[threadIdx.x >> 5];
-  uint32_t head = 0, tail = 0;
   unsigned long long nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
-  for (uint32_t tile = blockIdx.x * wpb + (threadIdx.x >> 5); tile < tiles; tile += gridDim.x * wpb)
-    run_tile<R, S, V>(P, p, tile << 5, n, ring, head, tail, nsteps, ncreated);
-  if (tail != head) drain<R, S>(P, p, ring, head, tail - head, ncreated);
+  run_tiles<R, S, V>(P, p, blockIdx.x * wpb + (threadIdx.x >> 5), tiles, gridDim.x * wpb, n, ring, nsteps, ncreated);
   if ((threadIdx.x & 31) == 0) {
     if (nsteps[S]) atomicAdd(&s_steps, nsteps[S]);
     for (int k = 0; k < 3; ++k)
