@@ -376,88 +376,67 @@ template <class R> struct WarpRing {
   uint32_t ev[kRing], pstep[kRing], nav[kRing], proc[kRing];
 };
 
-template <class R, int S>
-__device__ __forceinline__ void drain(const Params& P, int p, WarpRing<R>& ring, uint32_t head, uint32_t count,
-                                      unsigned long long* ncreated) {
-  const int lane = threadIdx.x & 31;
-  const bool have = (uint32_t)lane < count;
-  Trk<R> t;
-  t.nav = 0; t.ev = 0; t.id = 0; t.E = 0.0; t.step = 0;
-  uint32_t pstep = 0;
-  Ixn<R> sec;
-  sec.n = 0;
-  bool alive = false;
-  if (have) {
-    const uint32_t j = (head + lane) & (kRing - 1);
-    t.x = ring.x[j]; t.y = ring.y[j]; t.z = ring.z[j]; t.E = ring.E[j];
-    t.u[0] = ring.ux[j]; t.u[1] = ring.uy[j]; t.u[2] = ring.uz[j];
-    t.id = ring.id[j]; t.ev = ring.ev[j]; t.nav = ring.nav[j];
-    pstep = ring.pstep[j];
-    t.step = pstep + 1;
-    double dep = 0.0;
-    alive = step_interact<R, S>(P, t, pstep, (int)ring.proc[j], sec, dep);
-    score(P, t.ev, __ldg(P.geo.vol_bin + (int)(t.nav & 0xFFFFu)), dep);
-  }
-  __syncwarp();
-  emit<R, S>(P, p, t, alive, sec, pstep, ncreated);
-}
-
-// One warp takes 32 consecutive tracks of species S: phase A for each, appends the
-// survivors and queues the interactions.
-template <class R, int S, int V = 0>
-__device__ __forceinline__ void run_tile(const Params& P, int p, uint32_t base, uint32_t n, WarpRing<R>& ring,
-                                         uint32_t& tail, unsigned long long* nsteps, unsigned long long* ncreated) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t i = base + lane;
-  const bool active = i < n;
-  Trk<R> t;
-  t.nav = 0; t.ev = 0; t.id = 0; t.E = 0.0;
-  Ixn<R> sec;
-  sec.n = 0;
-  uint32_t pstep = 0;
-  int outcome = kDead, proc = 0;
-  if (active) {
-    load_track<R>(P.qd[3 * p + S], i, t);
-    double dep = 0.0;
-    int dep_bin = -1;
-    outcome = step_transport<R, S, V>(P, t, sec, dep, dep_bin, pstep, proc);
-    // S10: score the step's deposit in (event, layer, material)
-    score(P, t.ev, dep_bin, dep);
-  }
-  nsteps[S] += __popc(__ballot_sync(0xFFFFFFFFu, active));
-  emit<R, S>(P, p, t, outcome == kAlive, sec, pstep, ncreated);
-  const uint32_t need = __ballot_sync(0xFFFFFFFFu, outcome == kInteract);
-  if (outcome == kInteract) {
-    const uint32_t j = (tail + __popc(need & ((1u << lane) - 1u))) & (kRing - 1);
-    ring.x[j] = t.x; ring.y[j] = t.y; ring.z[j] = t.z; ring.E[j] = t.E;
-    ring.ux[j] = t.u[0]; ring.uy[j] = t.u[1]; ring.uz[j] = t.u[2];
-    ring.id[j] = t.id; ring.ev[j] = t.ev; ring.nav[j] = t.nav; ring.pstep[j] = pstep; ring.proc[j] = (uint32_t)proc;
-  }
-  tail += __popc(need);
-  __syncwarp();
-}
-
-// All of one warp's tiles of species S (tile, tile + stride, ... below tiles): phase A tile
-// by tile, a full warp of interactions whenever 32 wait, and the rest at the end. Phase A
-// and the interactions each have one call site, so the samplers are inlined once per kernel.
+// All of one warp's tiles of species S (tile, tile + stride, ... below tiles). Each pass of
+// the loop is either phase A of the next tile (load, step to the next boundary or
+// interaction, queue the interactions in the ring) or, once 32 wait or no tile is left, a
+// warp of up to 32 queued interactions. Both share the scoring and the appends, so every
+// part of the step is inlined once per kernel (smaller code: fewer instruction-cache
+// misses).
 template <class R, int S, int V = 0>
 __device__ __forceinline__ void run_tiles(const Params& P, int p, uint32_t tile, uint32_t tiles, uint32_t stride,
                                           uint32_t n, WarpRing<R>& ring, unsigned long long* nsteps,
                                           unsigned long long* ncreated) {
+  const uint32_t lane = threadIdx.x & 31;
   uint32_t head = 0, tail = 0;
   for (;;) {
     const uint32_t waiting = tail - head;
-    if (waiting < 32u) {
-      if (tile < tiles) {
-        run_tile<R, S, V>(P, p, tile << 5, n, ring, tail, nsteps, ncreated);
-        tile += stride;
-        continue;
+    const bool phase_a = waiting < 32u && tile < tiles;  // warp-uniform
+    if (!phase_a && waiting == 0u) break;
+    const uint32_t c = phase_a ? 0u : min(waiting, 32u);
+    Trk<R> t;
+    t.nav = 0; t.ev = 0; t.id = 0; t.E = 0.0; t.step = 0;
+    Ixn<R> sec;
+    sec.n = 0;
+    uint32_t pstep = 0;
+    int outcome = kDead, proc = 0, bin = -1;
+    double dep = 0.0;
+    if (phase_a) {
+      const uint32_t i = (tile << 5) + lane;
+      const bool active = i < n;
+      if (active) {
+        load_track<R>(P.qd[3 * p + S], i, t);
+        outcome = step_transport<R, S, V>(P, t, sec, dep, bin, pstep, proc);
       }
-      if (waiting == 0u) break;
+      nsteps[S] += __popc(__ballot_sync(0xFFFFFFFFu, active));
+    } else if (lane < c) {
+      const uint32_t j = (head + lane) & (kRing - 1);
+      t.x = ring.x[j]; t.y = ring.y[j]; t.z = ring.z[j]; t.E = ring.E[j];
+      t.u[0] = ring.ux[j]; t.u[1] = ring.uy[j]; t.u[2] = ring.uz[j];
+      t.id = ring.id[j]; t.ev = ring.ev[j]; t.nav = ring.nav[j];
+      pstep = ring.pstep[j];
+      t.step = pstep + 1;
+      outcome = step_interact<R, S>(P, t, pstep, (int)ring.proc[j], sec, dep) ? kAlive : kDead;
+      bin = __ldg(P.geo.vol_bin + (int)(t.nav & 0xFFFFu));
     }
-    const uint32_t c = min(waiting, 32u);
-    drain<R, S>(P, p, ring, head, c, ncreated);
-    head += c;
+    // S10: score the step's deposit in (event, layer, material)
+    score(P, t.ev, bin, dep);
+    __syncwarp();
+    emit<R, S>(P, p, t, outcome == kAlive, sec, pstep, ncreated);
+    if (phase_a) {
+      const uint32_t need = __ballot_sync(0xFFFFFFFFu, outcome == kInteract);
+      if (outcome == kInteract) {
+        const uint32_t j = (tail + __popc(need & ((1u << lane) - 1u))) & (kRing - 1);
+        ring.x[j] = t.x; ring.y[j] = t.y; ring.z[j] = t.z; ring.E[j] = t.E;
+        ring.ux[j] = t.u[0]; ring.uy[j] = t.u[1]; ring.uz[j] = t.u[2];
+        ring.id[j] = t.id; ring.ev[j] = t.ev; ring.nav[j] = t.nav; ring.pstep[j] = pstep;
+        ring.proc[j] = (uint32_t)proc;
+      }
+      tail += __popc(need);
+      tile += stride;
+    } else {
+      head += c;
+    }
+    // the next pass may write ring entries that lanes of this one read
     __syncwarp();
   }
 }
