@@ -43,8 +43,8 @@ TRACK_BYTES_SPLIT = 64  # x,y,z f64 + direction 3 f32 + E f64 + id u64 + event, 
 # DRAM bytes (read + write) per tracked step of the three transport kernels, from the ncu
 # capture of generation 60 (profiles/transport_kernels_10gev_e_showers_gen60_full.md);
 # valid while the kernel sources hash to NCU_SRC_HASH, null otherwise
-NCU_BYTES_PER_STEP = 113.3
-NCU_SRC_HASH = "87c9e016beaece3e"
+NCU_BYTES_PER_STEP = 112.5
+NCU_SRC_HASH = "3ce74fd6cb49f9ce"
 
 
 def kernel_src_hash() -> str:
