@@ -70,6 +70,7 @@ def args_parse():
     ap.add_argument("--arena-gb", type=float, default=10.0)
     ap.add_argument("--bps", type=int, default=0, help="transport-kernel blocks/SM variant (0 = library default)")
     ap.add_argument("--bps-species", type=str, default="", help="per-species variants gamma,e-,e+")
+    ap.add_argument("--block", type=int, default=0, help="threads per transport block (0 = tuned)")
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "rt", "batch"],
                     help="c2 (default) is the headline line; the others are the configuration studies")
     ap.add_argument("--seconds", type=float, default=20.0, help="serving workload duration")
@@ -245,6 +246,8 @@ def run_ours(a):
         launch_opts["blocks_per_sm_species"] = (A.C.c_int32 * 3)(*[int(x) for x in a.bps_species.split(",")])
     if a.graph:
         launch_opts["graph_generations"] = a.graph
+    if a.block:
+        launch_opts["block_size"] = a.block
     if a.fused >= 0:
         launch_opts["fused"] = a.fused
     if a.physics:

@@ -112,7 +112,7 @@ def main(argv=None):
     build.build()
     out = load()
     jobs = [(W.slab_calorimeter(), W.electrons(10000, 1e4), 1, 0.0),
-            (W.slab_calorimeter(), W.electrons(2000, 1e4), 0, 0.0),
+            (W.slab_calorimeter(), W.electrons(10000, 1e4), 0, 0.0),
             (W.barrel_calorimeter(), W.barrel_primaries(10000, seed=4), 1, 3.8)]
     for geom, prim, precision, field in jobs:
         k = key(geom.kind, precision)
