@@ -140,9 +140,8 @@ typedef struct {
   double tracks_per_MeV;      /* admission estimate of peak live tracks per MeV [0.25] */
   int32_t flags;              /* ADEPT_FLAG_* bits [0] */
   int32_t blocks_per_sm_species[3]; /* per-species override of blocks_per_sm (gamma, e-, e+) [0] */
-  int32_t fused;              /* 0: per generation, three species kernels run concurrently
-                                 and a close kernel follows them; 1: one kernel per generation
-                                 for all three species, whose last block closes the generation;
+  int32_t fused;              /* 0: per generation, three species kernels run concurrently;
+                                 1: one kernel per generation for all three species;
                                  blocks_per_sm picks its variant (2 or 3 split, 1 or 2 FP64) [0] */
   uint32_t physics;           /* ADEPT_PHYS_* bits [0] */
   double msc_range_factor;    /* f of the multiple-scattering step limit [0.04] */

@@ -657,31 +657,32 @@ static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b, bool captu
       if (e == cudaSuccess) e = cudaStreamWaitEvent(ts, c->fork, 0);
       if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev[4 * k], ts, rf);
     }
-    if (c->opt.fused) {  // one kernel per generation; its last block closes it
-      if (e == cudaSuccess) e = launch_fused_generation(c->P, c->opt.precision, c->fminb, c->fgrid, c->block, c->stream);
+    if (c->opt.fused) {  // one kernel per generation
+      if (e == cudaSuccess)
+        e = launch_fused_generation(c->P, (uint32_t)k, c->opt.precision, c->fminb, c->fgrid, c->block, c->stream);
       if (T) time_end(c->stream, c->kdone[0], 4 * k + 1);
       continue;
     }
-    // fork e- (main stream), e+ and gamma (side streams), join, close
+    // fork e- (main stream), e+ and gamma (side streams), join
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->side[j], c->fork, 0);
     cudaStream_t st[3] = {c->side[1], c->stream, c->side[0]};  // gamma, e-, e+
     // launch order e-, e+, gamma: measured 2 % faster than gamma first on the 10 GeV showers
     // (the gamma kernel, the largest, then fills the SMs as the charged kernels drain)
     for (int sp : {1, 2, 0}) {
-      if (e == cudaSuccess) e = launch_transport(c->P, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, st[sp]);
+      if (e == cudaSuccess)
+        e = launch_transport(c->P, (uint32_t)k, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, st[sp]);
       if (TS) time_end(st[sp], c->kdone[sp], 4 * k + 1 + sp);
     }
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventRecord(c->join[j], c->side[j]);
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->stream, c->join[j], 0);
     // without the per-species split: one end event once all three kernels have ended
     if (T && !TS) time_end(c->stream, c->kdone[0], 4 * k + 1);
-    if (e == cudaSuccess) e = launch_close_generation(c->P, c->stream);
   }
   if (T && e == cudaSuccess) {
     e = cudaEventRecord(c->tjoin, ts);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->tjoin, 0);
   }
-  if (e == cudaSuccess) e = launch_finish(c->P, b, c->stream);
+  if (e == cudaSuccess) e = launch_finish(c->P, b, gens, c->stream);
   return e;
 }
 
@@ -720,7 +721,7 @@ static int launch_chunk(adept_ctx* c, int b) {
   } else {
     CK(enqueue_generations(c, 1, b, false));
   }
-  c->stats.launches += (c->opt.fused ? 1 : 4) * gens + 2;
+  c->stats.launches += (c->opt.fused ? 1 : 3) * gens + 3;
   CK(cudaMemcpyAsync(c->h_ctrl[b], c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_done[b], c->P.evt.done_list[b], sizeof(uint32_t) * kDoneChunk, cudaMemcpyDeviceToHost,
                      c->stream));
@@ -892,7 +893,7 @@ extern "C" int adept_transport(adept_ctx* c, uint64_t timeout_us) {
         if (rc) return rc;
       }
     }
-    const uint32_t live = h.count[h.gen & 1][0] + h.count[h.gen & 1][1] + h.count[h.gen & 1][2];
+    const uint32_t live = h.count[h.gen % 3][0] + h.count[h.gen % 3][1] + h.count[h.gen % 3][2];
     idle_chunks = (live == 0 && done.empty()) ? idle_chunks + 1 : 0;
     if (idle_chunks > 8) {
       std::lock_guard<std::mutex> lk(c->mu);

@@ -2,11 +2,10 @@
 //
 // Every warp takes the 32-track tiles of the concatenated gamma, e- and e+ queues in a
 // warp-strided order, species by species, in three consecutive loops (so that the register
-// allocation of one species' step does not overlap another's). The last block to finish
-// closes the generation (publishes the next queue sizes and advances gen); nothing waits
-// for anything, so the kernel needs no co-residency. Chained in a CUDA graph this is one
-// kernel node per generation instead of a fork, three species kernels, a join and a close
-// kernel, and the species share the SMs until the generation's last tile.
+// allocation of one species' step does not overlap another's). Nothing waits for anything,
+// so the kernel needs no co-residency. Chained in a CUDA graph this is one kernel node per
+// generation instead of a fork, three species kernels and a join, and the species share
+// the SMs until the generation's last tile.
 #include <cuda_runtime.h>
 
 #include "layout.h"
@@ -23,43 +22,38 @@ __device__ __forceinline__ uint32_t next_first(uint32_t first, uint32_t len, uin
 }
 
 template <class R, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_fused_generation(Params P) {
+__global__ void __launch_bounds__(256, MINB) k_fused_generation(Params P, uint32_t gk) {
   __shared__ WarpRing<R> rings[8];
   __shared__ unsigned long long s_cnt[6];
   WarpRing<R>& ring = rings[threadIdx.x >> 5];
+  const uint32_t gen = __ldcg(&P.ctrl->gen) + gk;
   if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) open_generation(P, gen, gk);
   __syncthreads();
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t nwarps = gridDim.x * wpb;
-  const int p = __ldcg(&P.ctrl->gen) & 1;
-  const uint32_t n0 = min(__ldcg(&P.ctrl->count[p][0]), P.cap);
-  const uint32_t n1 = min(__ldcg(&P.ctrl->count[p][1]), P.cap);
-  const uint32_t n2 = min(__ldcg(&P.ctrl->count[p][2]), P.cap);
+  const int p = gen & 1, cr = gen % 3, cw = (gen + 1) % 3;
+  const uint32_t n0 = min(__ldcg(&P.ctrl->count[cr][0]), P.cap);
+  const uint32_t n1 = min(__ldcg(&P.ctrl->count[cr][1]), P.cap);
+  const uint32_t n2 = min(__ldcg(&P.ctrl->count[cr][2]), P.cap);
   const uint32_t T0 = (n0 + 31) >> 5, T1 = (n1 + 31) >> 5, T2 = (n2 + 31) >> 5;
-  unsigned long long nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
+  uint32_t nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};  // per warp, this generation
   uint32_t first = blockIdx.x * wpb + (threadIdx.x >> 5);
-  run_tiles<R, 0>(P, p, first, T0, nwarps, n0, ring, nsteps, ncreated);
+  run_tiles<R, 0>(P, p, cw, first, T0, nwarps, n0, ring, nsteps, ncreated);
   first = next_first(first, T0, nwarps);
-  run_tiles<R, 1>(P, p, first, T1, nwarps, n1, ring, nsteps, ncreated);
+  run_tiles<R, 1>(P, p, cw, first, T1, nwarps, n1, ring, nsteps, ncreated);
   first = next_first(first, T1, nwarps);
-  run_tiles<R, 2>(P, p, first, T2, nwarps, n2, ring, nsteps, ncreated);
+  run_tiles<R, 2>(P, p, cw, first, T2, nwarps, n2, ring, nsteps, ncreated);
   if ((threadIdx.x & 31) == 0)
     for (int k = 0; k < 3; ++k) {
-      if (nsteps[k]) atomicAdd(&s_cnt[k], nsteps[k]);
-      if (ncreated[k]) atomicAdd(&s_cnt[3 + k], ncreated[k]);
+      if (nsteps[k]) atomicAdd(&s_cnt[k], (unsigned long long)nsteps[k]);
+      if (ncreated[k]) atomicAdd(&s_cnt[3 + k], (unsigned long long)ncreated[k]);
     }
   __syncthreads();
   if (threadIdx.x != 0) return;
   for (int k = 0; k < 3; ++k) {
     if (s_cnt[k]) atomicAdd(&P.ctrl->steps[k], s_cnt[k]);
     if (s_cnt[3 + k]) atomicAdd(&P.ctrl->created[k], s_cnt[3 + k]);
-  }
-  // last block out closes the generation (its appends and every other block's are
-  // ordered before the ticket by the fence)
-  __threadfence();
-  if (atomicAdd(&P.ctrl->blocks_done, 1u) == gridDim.x - 1) {
-    P.ctrl->blocks_done = 0;
-    close_generation(P);
   }
 }
 
@@ -75,8 +69,9 @@ int fused_max_blocks_per_sm(int precision, int minb, int block) {
   return n;
 }
 
-cudaError_t launch_fused_generation(const Params& P, int precision, int minb, int grid, int block, cudaStream_t st) {
-  void* args[] = {const_cast<Params*>(&P)};
+cudaError_t launch_fused_generation(const Params& P, uint32_t gk, int precision, int minb, int grid, int block,
+                                    cudaStream_t st) {
+  void* args[] = {const_cast<Params*>(&P), &gk};
   return cudaLaunchKernel(fused_fn(precision, minb), dim3(grid), dim3(block), args, 0, st);
 }
 

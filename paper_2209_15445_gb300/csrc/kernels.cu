@@ -196,16 +196,6 @@ cudaError_t launch_build_tables(const Params& P, const double* mat_in, int n_mat
   return cudaGetLastError();
 }
 
-// The three species kernels of a generation run concurrently; this closes it after them.
-__global__ void k_close_generation(Params P) {
-  if (threadIdx.x == 0) close_generation(P);
-}
-
-cudaError_t launch_close_generation(const Params& P, cudaStream_t st) {
-  k_close_generation<<<1, 32, 0, st>>>(P);
-  return cudaGetLastError();
-}
-
 // Each species kernel is compiled for 1..4 resident blocks of 256 threads per SM
 // (register caps 255, 128, 85, 64); the choice trades occupancy against spills.
 template <class R, int S>
@@ -235,9 +225,9 @@ int transport_max_blocks_per_sm(int precision, int species, int minb, int block,
   return n;
 }
 
-cudaError_t launch_transport(const Params& P, int precision, int species, int minb, int grid, int block,
+cudaError_t launch_transport(const Params& P, uint32_t gk, int precision, int species, int minb, int grid, int block,
                              cudaStream_t st) {
-  void* args[] = {const_cast<Params*>(&P)};
+  void* args[] = {const_cast<Params*>(&P), &gk};
   return cudaLaunchKernel(pick_transport(precision, species, minb, transport_variant(P)), dim3(grid), dim3(block), args,
                           0, st);
 }
@@ -278,8 +268,9 @@ __global__ void k_init_primaries(Params P, const TrackIn* recs, const uint32_t* 
     record_leak(P, r.pdg, slot, r.E, r.pos[0], r.pos[1], r.pos[2], r.dir[0], r.dir[1], r.dir[2]);
     return;
   }
-  const int p = __ldcg(&P.ctrl->gen) & 1;
-  const uint32_t d = atomicAdd(&P.ctrl->count[p][sp], 1u);
+  const uint32_t gen = __ldcg(&P.ctrl->gen);
+  const int p = gen & 1;
+  const uint32_t d = atomicAdd(&P.ctrl->count[gen % 3][sp], 1u);
   if (d >= P.cap) {
     atomicAdd(&P.ctrl->overflow, 1ull);
     atomicAdd(P.evt.killed + slot, r.E + rest);
@@ -298,14 +289,29 @@ cudaError_t launch_init_primaries(const Params& P, const TrackIn* recs, const ui
 }
 
 // ======================================================================== completion
+// End of a chunk of `gens` generations: log the sizes its last generation left, and advance
+// gen and the generation count. One thread.
+__global__ void k_end_chunk(Params P, uint32_t gens) {
+  if (threadIdx.x != 0) return;
+  volatile Ctrl* c = P.ctrl;
+  const uint32_t gen = c->gen + gens;
+  const uint32_t ln = c->log_n;
+  if (ln < P.max_log) {
+    for (int k = 0; k < 3; ++k) P.gen_log[3 * ln + k] = min(c->count[gen % 3][k], P.cap);
+    c->log_n = ln + 1;
+  }
+  c->generations = c->generations + gens;
+  c->gen = gen;
+}
+
 // An event is finished when no live track of it is left in the current queues: mark
 // the slots that still have tracks with the current generation, then every active slot
 // not marked is done and goes to the done list.
 __global__ void k_mark(Params P) {
   const uint32_t gen = __ldcg(&P.ctrl->gen);
-  const int p = gen & 1;
-  const uint32_t n0 = min(__ldcg(&P.ctrl->count[p][0]), P.cap), n1 = min(__ldcg(&P.ctrl->count[p][1]), P.cap),
-                 n2 = min(__ldcg(&P.ctrl->count[p][2]), P.cap);
+  const int p = gen & 1, cr = gen % 3;
+  const uint32_t n0 = min(__ldcg(&P.ctrl->count[cr][0]), P.cap), n1 = min(__ldcg(&P.ctrl->count[cr][1]), P.cap),
+                 n2 = min(__ldcg(&P.ctrl->count[cr][2]), P.cap);
   const uint32_t total = n0 + n1 + n2;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int sp = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);
@@ -327,7 +333,8 @@ __global__ void k_finish(Params P, int b) {
   }
 }
 
-cudaError_t launch_finish(const Params& P, int b, cudaStream_t st) {
+cudaError_t launch_finish(const Params& P, int b, int gens, cudaStream_t st) {
+  k_end_chunk<<<1, 32, 0, st>>>(P, (uint32_t)gens);
   k_mark<<<1216, 256, 0, st>>>(P);
   k_finish<<<(P.evt.max_slots + 255) / 256 < 1216 ? (P.evt.max_slots + 255) / 256 : 1216, 256, 0, st>>>(P, b);
   return cudaGetLastError();

@@ -71,13 +71,15 @@ struct TrackSoA {
   uint4* meta;     // id lo, id hi, event slot, step
 };
 
-// Device control block: queue sizes for the two buffer parities, generation counter,
-// statistics and the done-event list of the last chunk. Written by kernels, read by
-// the host after each chunk.
+// Device control block: queue sizes, generation counter, statistics and the done-event
+// list of the last chunk. Written by kernels, read by the host after each chunk.
+// Generation g reads the track buffers of parity g & 1 and the sizes count[g % 3], and
+// appends to parity (g + 1) & 1 and count[(g + 1) % 3]. Three size slots let one thread of
+// generation g empty count[(g + 2) % 3] (read by generation g - 1, appended to by g + 1)
+// without a separate close step between generations.
 struct Ctrl {
-  uint32_t gen;               // generations run; parity gen & 1 holds the current queues
-  uint32_t count[2][3];       // queue sizes [parity][species]
-  uint32_t blocks_done;       // finished blocks of the fused generation kernel (last one closes)
+  uint32_t gen;               // generations run before the current chunk (advanced at its end)
+  uint32_t count[3][3];       // queue sizes [generation mod 3][species]
   uint32_t done_count[2];     // events found finished by the finish pass of a chunk (per buffer)
   uint32_t log_n;             // rows written to the generation log
   uint32_t error;             // first device-detected error code (0 = none)
@@ -156,16 +158,17 @@ cudaError_t launch_build_tables(const Params& P, const double* mat_in, int n_mat
                                 MatDev* mat, BuildScratch s, double2* g64, double2* e64, double2* p64,
                                 float2* g32, float2* e32, float2* p32, double* re64, double* rp64,
                                 float* re32, float* rp32, double* Tc, double* kc, cudaStream_t st);
-// one generation of one species (the three may run concurrently), then the close
-cudaError_t launch_transport(const Params& P, int precision, int species, int minb, int grid, int block,
+// generation gen + gk of one species (gk: its place in the chunk; the three species of a
+// generation may run concurrently)
+cudaError_t launch_transport(const Params& P, uint32_t gk, int precision, int species, int minb, int grid, int block,
                              cudaStream_t st);
-cudaError_t launch_close_generation(const Params& P, cudaStream_t st);
 cudaError_t launch_admit(const Params& P, uint32_t slot_base, const uint32_t* keys, int n_slots,
                          cudaStream_t st);
 // meta: per track (event index within the request, track id)
 cudaError_t launch_init_primaries(const Params& P, const TrackIn* recs, const uint32_t* meta, int n,
                                   uint32_t slot_base, int precision, cudaStream_t st);
-cudaError_t launch_finish(const Params& P, int buffer, cudaStream_t st);
+// end of a chunk of `gens` generations: log the last one, advance gen, find finished events
+cudaError_t launch_finish(const Params& P, int buffer, int gens, cudaStream_t st);
 cudaError_t launch_probe_philox(const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out,
                                 cudaStream_t st);
 cudaError_t launch_probe_interp(const Params& P, int s, int t, int m, int prec, const double* E, int n,
@@ -195,8 +198,9 @@ cudaError_t launch_probe_chord(const Params& P, int prec, const double* pos, con
                                const double* T, const int* q, const double* s_phys, int n, double* out, cudaStream_t st);
 cudaError_t launch_probe_continuous(const Params& P, int which, int species, int m, int prec, double T, double s,
                                     uint32_t event, int n, double* out, cudaStream_t st);
-// one kernel per generation for all species; its last block closes the generation
-cudaError_t launch_fused_generation(const Params& P, int precision, int minb, int grid, int block, cudaStream_t st);
+// generation gen + gk of all species in one kernel
+cudaError_t launch_fused_generation(const Params& P, uint32_t gk, int precision, int minb, int grid, int block,
+                                    cudaStream_t st);
 int fused_max_blocks_per_sm(int precision, int minb, int block);
 
 }  // namespace adept

@@ -314,8 +314,8 @@ __device__ __forceinline__ void score(const Params& P, uint32_t ev, int bin, dou
 // surviving track (alive) and up to two secondaries, and gets consecutive slots of the
 // next queues through one atomic per species per warp.
 template <class R, int S>
-__device__ __forceinline__ void emit(const Params& P, int p, const Trk<R>& t, bool alive, const Ixn<R>& sec,
-                                     uint32_t pstep, unsigned long long* ncreated) {
+__device__ __forceinline__ void emit(const Params& P, int p, int cw, const Trk<R>& t, bool alive, const Ixn<R>& sec,
+                                     uint32_t pstep, uint32_t* ncreated) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const bool f1 = sec.n > 0 && sec.sp[0] >= 0;
@@ -329,7 +329,7 @@ __device__ __forceinline__ void emit(const Params& P, int p, const Trk<R>& t, bo
     b2[k] = __ballot_sync(0xFFFFFFFFu, s2 == k);
     const uint32_t cnt = __popc(b0[k]) + __popc(b1[k]) + __popc(b2[k]);
     uint32_t bk = 0;
-    if (lane == 0 && cnt) bk = atomicAdd(&P.ctrl->count[p ^ 1][k], cnt);
+    if (lane == 0 && cnt) bk = atomicAdd(&P.ctrl->count[cw][k], cnt);
     wbase[k] = __shfl_sync(0xFFFFFFFFu, bk, 0);
     ncreated[k] += __popc(b1[k]) + __popc(b2[k]);
   }
@@ -383,9 +383,8 @@ template <class R> struct WarpRing {
 // part of the step is inlined once per kernel (smaller code: fewer instruction-cache
 // misses).
 template <class R, int S, int V = 0>
-__device__ __forceinline__ void run_tiles(const Params& P, int p, uint32_t tile, uint32_t tiles, uint32_t stride,
-                                          uint32_t n, WarpRing<R>& ring, unsigned long long* nsteps,
-                                          unsigned long long* ncreated) {
+__device__ __forceinline__ void run_tiles(const Params& P, int p, int cw, uint32_t tile, uint32_t tiles, uint32_t stride,
+                                          uint32_t n, WarpRing<R>& ring, uint32_t* nsteps, uint32_t* ncreated) {
   const uint32_t lane = threadIdx.x & 31;
   uint32_t head = 0, tail = 0;
   for (;;) {
@@ -421,7 +420,7 @@ __device__ __forceinline__ void run_tiles(const Params& P, int p, uint32_t tile,
     // S10: score the step's deposit in (event, layer, material)
     score(P, t.ev, bin, dep);
     __syncwarp();
-    emit<R, S>(P, p, t, outcome == kAlive, sec, pstep, ncreated);
+    emit<R, S>(P, p, cw, t, outcome == kAlive, sec, pstep, ncreated);
     if (phase_a) {
       const uint32_t need = __ballot_sync(0xFFFFFFFFu, outcome == kInteract);
       if (outcome == kInteract) {
@@ -441,63 +440,59 @@ __device__ __forceinline__ void run_tiles(const Params& P, int p, uint32_t tile,
   }
 }
 
+// The bookkeeping between generations, done by one thread of generation g while it runs:
+// empty the size slot that generation g + 1 appends to (its last reader, generation g - 1,
+// has ended), and log the sizes generation g - 1 left (final once it ended). gk = 0 (the
+// first generation of a chunk) leaves the log to the end of the previous chunk.
+__device__ __forceinline__ void open_generation(const Params& P, uint32_t gen, uint32_t gk) {
+  volatile Ctrl* c = P.ctrl;
+  const uint32_t cz = (gen + 2) % 3, cr = gen % 3;
+  for (int k = 0; k < 3; ++k) c->count[cz][k] = 0;
+  if (gk == 0) return;
+  const uint32_t ln = c->log_n;
+  if (ln < P.max_log) {
+    for (int k = 0; k < 3; ++k) P.gen_log[3 * ln + k] = min(c->count[cr][k], P.cap);
+    c->log_n = ln + 1;
+  }
+}
+
 // One generation of one species (paper Sec. 3: TransportElectrons, TransportPositrons and
 // TransportGammas). Persistent launch: each warp takes 32-track tiles of the current queue.
 // The three species kernels of a generation are independent (each reads its own current
 // queue and appends to the next ones atomically), so they run concurrently on three
-// streams; k_close_generation then publishes the next queue sizes.
+// streams, and the next generation's kernels start once all three have ended.
+// gk: the generation's place in its chunk (gen, advanced only between chunks, plus gk).
 // V: the variant of the step (see step_transport); variants.cu instantiates V = 1..3 for
 // e- and e+.
 template <class R, int S, int MINB, int V = 0>
-__global__ void __launch_bounds__(256, MINB) k_transport(Params P) {
+__global__ void __launch_bounds__(256, MINB) k_transport(Params P, uint32_t gk) {
   __shared__ unsigned long long s_steps, s_created[3];
   __shared__ WarpRing<R> rings[8];
-  const uint32_t gen = __ldcg(&P.ctrl->gen);
+  const uint32_t gen = __ldcg(&P.ctrl->gen) + gk;
   const int p = gen & 1;
   if (threadIdx.x == 0) { s_steps = 0; s_created[0] = s_created[1] = s_created[2] = 0; }
+  // the e- kernel is launched first of the three
+  if (S == 1 && blockIdx.x == 0 && threadIdx.x == 0) open_generation(P, gen, gk);
   __syncthreads();
   // injection may have counted past the capacity (those tracks were dropped)
-  const uint32_t n = min(__ldcg(&P.ctrl->count[p][S]), P.cap);
+  const uint32_t n = min(__ldcg(&P.ctrl->count[gen % 3][S]), P.cap);
   const uint32_t tiles = (n + 31) >> 5;
   const uint32_t wpb = blockDim.x >> 5;
   WarpRing<R>& ring = rings[threadIdx.x >> 5];
-  unsigned long long nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
-  run_tiles<R, S, V>(P, p, blockIdx.x * wpb + (threadIdx.x >> 5), tiles, gridDim.x * wpb, n, ring, nsteps, ncreated);
+  // per-warp counts of one generation (at most the queue capacity each: 32 bits suffice)
+  uint32_t nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};
+  run_tiles<R, S, V>(P, p, (gen + 1) % 3, blockIdx.x * wpb + (threadIdx.x >> 5), tiles, gridDim.x * wpb, n, ring,
+                     nsteps, ncreated);
   if ((threadIdx.x & 31) == 0) {
-    if (nsteps[S]) atomicAdd(&s_steps, nsteps[S]);
+    if (nsteps[S]) atomicAdd(&s_steps, (unsigned long long)nsteps[S]);
     for (int k = 0; k < 3; ++k)
-      if (ncreated[k]) atomicAdd(&s_created[k], ncreated[k]);
+      if (ncreated[k]) atomicAdd(&s_created[k], (unsigned long long)ncreated[k]);
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
   if (s_steps) atomicAdd(&P.ctrl->steps[S], s_steps);
   for (int k = 0; k < 3; ++k)
     if (s_created[k]) atomicAdd(&P.ctrl->created[k], s_created[k]);
-}
-
-// Close a generation once the species kernels are done: publish the next queue sizes
-// (clamped to the capacity; overflow was counted), log them, empty the consumed queues
-// and advance gen, whose parity selects the buffers. One thread runs it.
-__device__ __forceinline__ void close_generation(const Params& P) {
-  volatile Ctrl* c = P.ctrl;
-  const uint32_t gen = c->gen;
-  const int p = gen & 1;
-  uint32_t nn[3];
-  for (int k = 0; k < 3; ++k) {
-    uint32_t m = c->count[p ^ 1][k];
-    if (m > P.cap) m = P.cap;
-    nn[k] = m;
-    c->count[p ^ 1][k] = m;
-    c->count[p][k] = 0;
-  }
-  const uint32_t ln = c->log_n;
-  if (ln < P.max_log) {
-    for (int k = 0; k < 3; ++k) P.gen_log[3 * ln + k] = nn[k];
-    c->log_n = ln + 1;
-  }
-  c->generations = c->generations + 1;
-  __threadfence();
-  c->gen = gen + 1;
 }
 
 }  // namespace adept

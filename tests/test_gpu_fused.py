@@ -1,5 +1,5 @@
-"""The fused mode (one kernel per generation for all three species, the last block closing
-the generation) against the FP64 oracle and against the concurrent species kernels.
+"""The fused mode (one kernel per generation for all three species) against the FP64
+oracle and against the concurrent species kernels.
 
 The random streams are keyed per track, so the set of tracks in each generation does not
 depend on which kernel or warp ran them: per-generation queue sizes must equal the
