@@ -659,7 +659,8 @@ static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b, bool captu
     }
     if (c->opt.fused) {  // one kernel per generation
       if (e == cudaSuccess)
-        e = launch_fused_generation(c->P, (uint32_t)k, c->opt.precision, c->fminb, c->fgrid, c->block, c->stream);
+        e = launch_fused_generation(c->P, (uint32_t)k, c->opt.precision, c->fminb, c->fgrid, c->block, k > 0,
+                                    c->stream);
       if (T) time_end(c->stream, c->kdone[0], 4 * k + 1);
       continue;
     }
@@ -670,7 +671,8 @@ static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b, bool captu
     // (the gamma kernel, the largest, then fills the SMs as the charged kernels drain)
     for (int sp : {1, 2, 0}) {
       if (e == cudaSuccess)
-        e = launch_transport(c->P, (uint32_t)k, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, st[sp]);
+        e = launch_transport(c->P, (uint32_t)k, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, k > 0,
+                             st[sp]);
       if (TS) time_end(st[sp], c->kdone[sp], 4 * k + 1 + sp);
     }
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventRecord(c->join[j], c->side[j]);

@@ -26,6 +26,8 @@ __global__ void __launch_bounds__(256, MINB) k_fused_generation(Params P, uint32
   __shared__ WarpRing<R> rings[8];
   __shared__ unsigned long long s_cnt[6];
   WarpRing<R>& ring = rings[threadIdx.x >> 5];
+  grid_dependency_wait();
+  allow_dependent_launch();
   const uint32_t gen = __ldcg(&P.ctrl->gen) + gk;
   if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) open_generation(P, gen, gk);
@@ -70,9 +72,18 @@ int fused_max_blocks_per_sm(int precision, int minb, int block) {
 }
 
 cudaError_t launch_fused_generation(const Params& P, uint32_t gk, int precision, int minb, int grid, int block,
-                                    cudaStream_t st) {
+                                    bool pdl, cudaStream_t st) {
   void* args[] = {const_cast<Params*>(&P), &gk};
-  return cudaLaunchKernel(fused_fn(precision, minb), dim3(grid), dim3(block), args, 0, st);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelExC(&cfg, fused_fn(precision, minb), args);
 }
 
 }  // namespace adept

@@ -226,10 +226,18 @@ int transport_max_blocks_per_sm(int precision, int species, int minb, int block,
 }
 
 cudaError_t launch_transport(const Params& P, uint32_t gk, int precision, int species, int minb, int grid, int block,
-                             cudaStream_t st) {
+                             bool pdl, cudaStream_t st) {
   void* args[] = {const_cast<Params*>(&P), &gk};
-  return cudaLaunchKernel(pick_transport(precision, species, minb, transport_variant(P)), dim3(grid), dim3(block), args,
-                          0, st);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelExC(&cfg, pick_transport(precision, species, minb, transport_variant(P)), args);
 }
 
 // ======================================================================== admission

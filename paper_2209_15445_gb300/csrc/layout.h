@@ -159,9 +159,10 @@ cudaError_t launch_build_tables(const Params& P, const double* mat_in, int n_mat
                                 float2* g32, float2* e32, float2* p32, double* re64, double* rp64,
                                 float* re32, float* rp32, double* Tc, double* kc, cudaStream_t st);
 // generation gen + gk of one species (gk: its place in the chunk; the three species of a
-// generation may run concurrently)
+// generation may run concurrently). pdl: launch with a programmatic dependency on the
+// stream's preceding kernels (the previous generation's), see grid_dependency_wait.
 cudaError_t launch_transport(const Params& P, uint32_t gk, int precision, int species, int minb, int grid, int block,
-                             cudaStream_t st);
+                             bool pdl, cudaStream_t st);
 cudaError_t launch_admit(const Params& P, uint32_t slot_base, const uint32_t* keys, int n_slots,
                          cudaStream_t st);
 // meta: per track (event index within the request, track id)
@@ -200,7 +201,7 @@ cudaError_t launch_probe_continuous(const Params& P, int which, int species, int
                                     uint32_t event, int n, double* out, cudaStream_t st);
 // generation gen + gk of all species in one kernel
 cudaError_t launch_fused_generation(const Params& P, uint32_t gk, int precision, int minb, int grid, int block,
-                                    cudaStream_t st);
+                                    bool pdl, cudaStream_t st);
 int fused_max_blocks_per_sm(int precision, int minb, int block);
 
 }  // namespace adept

@@ -440,6 +440,15 @@ __device__ __forceinline__ void run_tiles(const Params& P, int p, int cw, uint32
   }
 }
 
+// Programmatic dependent launch between generations: a generation's kernels may be
+// launched (and their blocks made resident) as soon as every block of the previous
+// generation's kernels has started, so that they wait on the SMs instead of being launched
+// after the previous generation ends. grid_dependency_wait() returns once the previous
+// generation's grids have completed and their writes are visible; both are no-ops for a
+// launch without programmatic dependencies.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // The bookkeeping between generations, done by one thread of generation g while it runs:
 // empty the size slot that generation g + 1 appends to (its last reader, generation g - 1,
 // has ended), and log the sizes generation g - 1 left (final once it ended). gk = 0 (the
@@ -468,6 +477,8 @@ template <class R, int S, int MINB, int V = 0>
 __global__ void __launch_bounds__(256, MINB) k_transport(Params P, uint32_t gk) {
   __shared__ unsigned long long s_steps, s_created[3];
   __shared__ WarpRing<R> rings[8];
+  grid_dependency_wait();
+  allow_dependent_launch();
   const uint32_t gen = __ldcg(&P.ctrl->gen) + gk;
   const int p = gen & 1;
   if (threadIdx.x == 0) { s_steps = 0; s_created[0] = s_created[1] = s_created[2] = 0; }
