@@ -40,11 +40,12 @@ UNIT = "tracked steps/s"
 WORKLOAD = ("10,000 x 10 GeV e- showers, 50-layer Pb 2.3 mm + lAr 5.7 mm slab calorimeter, 0.7 mm cut, "
             "no field; split precision, batched persistent launch with CUDA graphs")
 TRACK_BYTES_SPLIT = 64  # x,y,z f64 + direction 3 f32 + E f64 + id u64 + event, step, nav u32
-# DRAM bytes (read + write) per tracked step of the three transport kernels, from the ncu
-# capture of generation 60 (profiles/transport_kernels_10gev_e_showers_gen60_full.md);
-# valid while the kernel sources hash to NCU_SRC_HASH, null otherwise
-NCU_BYTES_PER_STEP = 112.5
-NCU_SRC_HASH = "3ce74fd6cb49f9ce"
+# DRAM bytes (read + write) per tracked step of the three concurrent transport kernels, from
+# the ncu captures of generation 60 (profiles/transport_kernels_10gev_e_showers_gen60_full.md
+# for the split form, profiles/transport_kernels_10gev_e_showers_fp64_gen60_full.md for the
+# plain FP64 form); valid while the kernel sources hash to NCU_SRC_HASH, null otherwise
+NCU_BYTES_PER_STEP = {1: 112.4, 0: 136.8}
+NCU_SRC_HASH = "23caeeb396701a74"
 
 
 def kernel_src_hash() -> str:
@@ -300,9 +301,9 @@ def run_ours(a):
     peak, peak_kind = peaks()
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9 if kern_ms > 0 else None
     traffic = None
-    # the ncu figure was taken on the split form's kernels; other forms report none
-    if NCU_BYTES_PER_STEP and a.precision == 1 and NCU_SRC_HASH == kernel_src_hash() and kern_n:
-        traffic = NCU_BYTES_PER_STEP * steps / kern_n
+    # the ncu figures were taken on the concurrent species kernels; the fused mode reports none
+    if a.precision in NCU_BYTES_PER_STEP and not tr.options.fused and NCU_SRC_HASH == kernel_src_hash() and kern_n:
+        traffic = NCU_BYTES_PER_STEP[a.precision] * steps / kern_n
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "kernel": ("k_fused_generation<%s> (one launch = one generation, all species)" if tr.options.fused else
