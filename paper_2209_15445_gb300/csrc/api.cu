@@ -895,7 +895,7 @@ extern "C" int adept_transport(adept_ctx* c, uint64_t timeout_us) {
         if (rc) return rc;
       }
     }
-    const uint32_t live = h.count[h.gen % 3][0] + h.count[h.gen % 3][1] + h.count[h.gen % 3][2];
+    const uint32_t live = h.count[h.gen % 3][0].n + h.count[h.gen % 3][1].n + h.count[h.gen % 3][2].n;
     idle_chunks = (live == 0 && done.empty()) ? idle_chunks + 1 : 0;
     if (idle_chunks > 8) {
       std::lock_guard<std::mutex> lk(c->mu);

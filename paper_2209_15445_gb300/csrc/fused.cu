@@ -35,9 +35,9 @@ __global__ void __launch_bounds__(256, MINB) k_fused_generation(Params P, uint32
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t nwarps = gridDim.x * wpb;
   const int p = gen & 1, cr = gen % 3, cw = (gen + 1) % 3;
-  const uint32_t n0 = min(__ldcg(&P.ctrl->count[cr][0]), P.cap);
-  const uint32_t n1 = min(__ldcg(&P.ctrl->count[cr][1]), P.cap);
-  const uint32_t n2 = min(__ldcg(&P.ctrl->count[cr][2]), P.cap);
+  const uint32_t n0 = min(__ldcg(&P.ctrl->count[cr][0].n), P.cap);
+  const uint32_t n1 = min(__ldcg(&P.ctrl->count[cr][1].n), P.cap);
+  const uint32_t n2 = min(__ldcg(&P.ctrl->count[cr][2].n), P.cap);
   const uint32_t T0 = (n0 + 31) >> 5, T1 = (n1 + 31) >> 5, T2 = (n2 + 31) >> 5;
   uint32_t nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};  // per warp, this generation
   uint32_t first = blockIdx.x * wpb + (threadIdx.x >> 5);

@@ -278,7 +278,7 @@ __global__ void k_init_primaries(Params P, const TrackIn* recs, const uint32_t* 
   }
   const uint32_t gen = __ldcg(&P.ctrl->gen);
   const int p = gen & 1;
-  const uint32_t d = atomicAdd(&P.ctrl->count[gen % 3][sp], 1u);
+  const uint32_t d = atomicAdd(&P.ctrl->count[gen % 3][sp].n, 1u);
   if (d >= P.cap) {
     atomicAdd(&P.ctrl->overflow, 1ull);
     atomicAdd(P.evt.killed + slot, r.E + rest);
@@ -305,7 +305,7 @@ __global__ void k_end_chunk(Params P, uint32_t gens) {
   const uint32_t gen = c->gen + gens;
   const uint32_t ln = c->log_n;
   if (ln < P.max_log) {
-    for (int k = 0; k < 3; ++k) P.gen_log[3 * ln + k] = min(c->count[gen % 3][k], P.cap);
+    for (int k = 0; k < 3; ++k) P.gen_log[3 * ln + k] = min(c->count[gen % 3][k].n, P.cap);
     c->log_n = ln + 1;
   }
   c->generations = c->generations + gens;
@@ -318,8 +318,8 @@ __global__ void k_end_chunk(Params P, uint32_t gens) {
 __global__ void k_mark(Params P) {
   const uint32_t gen = __ldcg(&P.ctrl->gen);
   const int p = gen & 1, cr = gen % 3;
-  const uint32_t n0 = min(__ldcg(&P.ctrl->count[cr][0]), P.cap), n1 = min(__ldcg(&P.ctrl->count[cr][1]), P.cap),
-                 n2 = min(__ldcg(&P.ctrl->count[cr][2]), P.cap);
+  const uint32_t n0 = min(__ldcg(&P.ctrl->count[cr][0].n), P.cap), n1 = min(__ldcg(&P.ctrl->count[cr][1].n), P.cap),
+                 n2 = min(__ldcg(&P.ctrl->count[cr][2].n), P.cap);
   const uint32_t total = n0 + n1 + n2;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int sp = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);

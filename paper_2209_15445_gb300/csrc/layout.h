@@ -77,9 +77,15 @@ struct TrackSoA {
 // appends to parity (g + 1) & 1 and count[(g + 1) % 3]. Three size slots let one thread of
 // generation g empty count[(g + 2) % 3] (read by generation g - 1, appended to by g + 1)
 // without a separate close step between generations.
+// A queue size on a 128-byte line of its own: every warp of a generation reserves its slots
+// with an atomic on one of these, and sizes sharing an L2 line would queue behind each other.
+struct alignas(128) QCount {
+  uint32_t n;
+  uint32_t pad[31];
+};
 struct Ctrl {
   uint32_t gen;               // generations run before the current chunk (advanced at its end)
-  uint32_t count[3][3];       // queue sizes [generation mod 3][species]
+  QCount count[3][3];         // queue sizes [generation mod 3][species]
   uint32_t done_count[2];     // events found finished by the finish pass of a chunk (per buffer)
   uint32_t log_n;             // rows written to the generation log
   uint32_t error;             // first device-detected error code (0 = none)

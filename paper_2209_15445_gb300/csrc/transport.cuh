@@ -329,7 +329,7 @@ __device__ __forceinline__ void emit(const Params& P, int p, int cw, const Trk<R
     b2[k] = __ballot_sync(0xFFFFFFFFu, s2 == k);
     const uint32_t cnt = __popc(b0[k]) + __popc(b1[k]) + __popc(b2[k]);
     uint32_t bk = 0;
-    if (lane == 0 && cnt) bk = atomicAdd(&P.ctrl->count[cw][k], cnt);
+    if (lane == 0 && cnt) bk = atomicAdd(&P.ctrl->count[cw][k].n, cnt);
     wbase[k] = __shfl_sync(0xFFFFFFFFu, bk, 0);
     ncreated[k] += __popc(b1[k]) + __popc(b2[k]);
   }
@@ -456,11 +456,11 @@ __device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddep
 __device__ __forceinline__ void open_generation(const Params& P, uint32_t gen, uint32_t gk) {
   volatile Ctrl* c = P.ctrl;
   const uint32_t cz = (gen + 2) % 3, cr = gen % 3;
-  for (int k = 0; k < 3; ++k) c->count[cz][k] = 0;
+  for (int k = 0; k < 3; ++k) c->count[cz][k].n = 0;
   if (gk == 0) return;
   const uint32_t ln = c->log_n;
   if (ln < P.max_log) {
-    for (int k = 0; k < 3; ++k) P.gen_log[3 * ln + k] = min(c->count[cr][k], P.cap);
+    for (int k = 0; k < 3; ++k) P.gen_log[3 * ln + k] = min(c->count[cr][k].n, P.cap);
     c->log_n = ln + 1;
   }
 }
@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(Params P, uint32_t gk) 
   if (S == 1 && blockIdx.x == 0 && threadIdx.x == 0) open_generation(P, gen, gk);
   __syncthreads();
   // injection may have counted past the capacity (those tracks were dropped)
-  const uint32_t n = min(__ldcg(&P.ctrl->count[gen % 3][S]), P.cap);
+  const uint32_t n = min(__ldcg(&P.ctrl->count[gen % 3][S].n), P.cap);
   const uint32_t tiles = (n + 31) >> 5;
   const uint32_t wpb = blockDim.x >> 5;
   WarpRing<R>& ring = rings[threadIdx.x >> 5];
