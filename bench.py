@@ -45,7 +45,7 @@ TRACK_BYTES_SPLIT = 64  # x,y,z f64 + direction 3 f32 + E f64 + id u64 + event, 
 # for the split form, profiles/transport_kernels_10gev_e_showers_fp64_gen60_full.md for the
 # plain FP64 form); valid while the kernel sources hash to NCU_SRC_HASH, null otherwise
 NCU_BYTES_PER_STEP = {1: 112.4, 0: 136.8}
-NCU_SRC_HASH = "23caeeb396701a74"
+NCU_SRC_HASH = "087a9c3e8e8c72cb"
 
 
 def kernel_src_hash() -> str:
