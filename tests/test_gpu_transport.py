@@ -87,6 +87,22 @@ def test_full_physics_generation_counts_bit_exact_few_events():
     tr.close()
 
 
+@pytest.mark.parametrize("chunk,fused", [(1, 0), (5, 0), (7, 1)])
+def test_generation_counts_across_chunk_lengths(chunk, fused):
+    """Generation g reads its queue sizes from slot g mod 3 and its tracks from buffer g mod 2,
+    and its place in the chunk comes in as an argument, so chunk lengths that are not
+    multiples of 6 start the chunks at every phase of both. The sizes per generation must
+    still equal the oracle's exactly (FP64), in both the concurrent and the fused mode."""
+    need_gpu()
+    geom = W.slab_calorimeter()
+    kw = dict(fused=1, blocks_per_sm=2) if fused else {}
+    tr = make(geom, precision=0, graph_generations=chunk, tuned=False, **kw)
+    prim = W.mixed(4, seed=23)
+    prim.E[:] = np.minimum(prim.E, 1000.0)
+    compare_generations(tr, oracle.Oracle(geom), prim, 0)
+    tr.close()
+
+
 def layer_check(g, o, frac=0.01, rel=0.01, nsig=3.0):
     """per-layer means within nsig combined SE and rel on layers above frac of the total"""
     mg, mo = g.mean(0), o.mean(0)
