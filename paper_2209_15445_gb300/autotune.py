@@ -67,7 +67,7 @@ def tune(geom, prim, precision, field_T=0.0, log=print):
     best = measure(geom, prim, precision, field_T, cfg)
     log(f"  start {cfg}: {best:.3e}")
     trials = [("graph_generations", v) for v in (16, 64)]
-    trials += [("block_size", 128)]
+    trials += [("block_size", v) for v in (64, 128)]  # 256 is the kernels' launch bound
     for sp in range(3):
         for v in (1, 2, 3, 4):
             trials.append((("blocks_per_sm_species", sp), v))
