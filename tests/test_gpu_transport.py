@@ -322,10 +322,12 @@ def test_admission_waits_for_slots_and_energy_budget():
     tr.close()
 
 
-def test_block_size_128_matches_oracle():
+@pytest.mark.parametrize("block", [64, 128])
+def test_small_blocks_match_oracle(block):
+    """the block sizes below 256 that the autotuner may pick"""
     need_gpu()
     geom = W.slab_calorimeter()
-    tr = make(geom, precision=0, block_size=128, graph_generations=16, tuned=False)
+    tr = make(geom, precision=0, block_size=block, graph_generations=16, tuned=False)
     prim = W.mixed(5, seed=24)
     prim.E[:] = np.minimum(prim.E, 1500.0)
     compare_generations(tr, oracle.Oracle(geom), prim, 0)
