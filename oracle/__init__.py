@@ -57,7 +57,7 @@ class _Result(C.Structure):
                 ("killed", C.POINTER(C.c_double)), ("steps", C.c_uint64 * 3),
                 ("created", C.c_uint64 * 3), ("gen_hist", C.POINTER(C.c_uint64)),
                 ("steplen_hist", C.POINTER(C.c_uint64)), ("leak_out", C.POINTER(C.c_double)),
-                ("leak_cap", C.c_uint64), ("leak_n", C.c_uint64)]
+                ("leak_cap", C.c_uint64), ("leak_n", C.c_uint64), ("boundary_steps", C.c_uint64 * 3)]
 
 
 def lib():
@@ -293,7 +293,8 @@ class Oracle:
         if rc != 0:
             raise ValueError("oracle transport rejected its input")
         out = dict(edep=edep, leaked=leaked, killed=killed, steps=np.array(list(res.steps), np.uint64),
-                   created=np.array(list(res.created), np.uint64))
+                   created=np.array(list(res.created), np.uint64),
+                   boundary_steps=np.array(list(res.boundary_steps), np.uint64))
         if max_gen > 0:
             out["gen_hist"] = gen
         if steplen:

@@ -1421,7 +1421,7 @@ typedef struct {
   uint32_t event;
   double* edep;  /* this event's bins */
   double leaked, killed;
-  uint64_t steps[3], created[3];
+  uint64_t steps[3], created[3], boundary[3];
   uint64_t* gen_hist; /* shared, atomically updated */
   uint64_t* steplen;  /* shared */
   or_result* res;     /* outgoing-particle list (shared, atomically indexed) */
@@ -1551,6 +1551,7 @@ static int step_track(ev_t* e, trk_t* t, stack_t_* st) {
   const double stot = sig[0] + sig[1] + sig[2];
   const double s_int = stot > 0.0 ? -log(u0) / stot : kInf;
   double s_phys = s_int;
+  int limited = 0; /* the step limit, not the sampled interaction length, ends the step */
   const int msc = (o->physics & OR_PHYS_MSC) != 0, fluct = (o->physics & OR_PHYS_FLUCT) != 0;
   if (q != 0 && m >= 0) {
     double smax = (R <= kRhoF) ? R : ((kAlphaR * R > kRhoF) ? kAlphaR * R : kRhoF);
@@ -1559,7 +1560,7 @@ static int step_track(ev_t* e, trk_t* t, stack_t_* st) {
       const double sm = (f * R > 0.01) ? f * R : 0.01;
       if (sm < smax) smax = sm;
     }
-    if (smax < s_phys) s_phys = smax;
+    if (smax < s_phys) { s_phys = smax; limited = 1; }
   }
 
   int next;
@@ -1627,8 +1628,11 @@ static int step_track(ev_t* e, trk_t* t, stack_t_* st) {
   if (boundary) {
     if (next < 0) { e->leaked += t->T + rest; record_leak(e, t); return 0; }
     t->vol = next;
+    e->boundary[sp]++;
     return 1;
   }
+  /* a step cut short by the step limit ends with its continuous loss only */
+  if (limited) return 1;
 
   /* discrete interaction: process chosen by u1 over the fixed order */
   const double x = u1 * stot;
@@ -1708,7 +1712,11 @@ static void run_event(job_t* j, int ev, stack_t_* st) {
   j->r->leaked[ev] = e.leaked;
   j->r->killed[ev] = e.killed;
   pthread_mutex_lock(&j->mu);
-  for (int s = 0; s < 3; ++s) { j->r->steps[s] += e.steps[s]; j->r->created[s] += e.created[s]; }
+  for (int s = 0; s < 3; ++s) {
+    j->r->steps[s] += e.steps[s];
+    j->r->created[s] += e.created[s];
+    j->r->boundary_steps[s] += e.boundary[s];
+  }
   pthread_mutex_unlock(&j->mu);
 }
 
@@ -1746,7 +1754,7 @@ int or_transport(const or_ctx* c, int n, const int* pdg, const double* E, const 
   }
   free(fill);
   memset(r->edep, 0, sizeof(double) * (size_t)n_events * c->n_bins);
-  for (int s = 0; s < 3; ++s) { r->steps[s] = 0; r->created[s] = 0; }
+  for (int s = 0; s < 3; ++s) { r->steps[s] = 0; r->created[s] = 0; r->boundary_steps[s] = 0; }
   pthread_mutex_init(&j.mu, NULL);
   int nt = o->n_threads > 0 ? o->n_threads : 1;
   if (nt > 256) nt = 256;

@@ -178,6 +178,7 @@ typedef struct {
   double* leak_out;
   uint64_t leak_cap;
   uint64_t leak_n;
+  uint64_t boundary_steps[3]; /* steps that ended on a boundary inside the world */
 } or_result;
 
 /* tracks: pdg (22, 11, -11), kinetic energy, position, direction, RNG event key, event slot */

@@ -178,6 +178,7 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
   R s_phys = stot > (R)0 ? M<R>::fdiv(-M<R>::flog(u0), stot) : M<R>::big();
   constexpr bool CH = (V & 1) != 0, PH = (V & 2) != 0 && S != 0;
   const bool msc = PH && (P.physics & 1u) != 0, fluct = PH && (P.physics & 2u) != 0;
+  bool limited = false;  // the step limit, not the sampled interaction length, ends the step
   if (q != 0 && m >= 0) {
     R smax = (Rr <= (R)kRhoF) ? Rr : ((R)kAlphaR * Rr > (R)kRhoF ? (R)kAlphaR * Rr : (R)kRhoF);
     if (PH && msc) {  // multiple-scattering step limit
@@ -185,7 +186,7 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
       const R sm = fR > (R)0.01 ? fR : (R)0.01;
       if (sm < smax) smax = sm;
     }
-    if (smax < s_phys) s_phys = smax;
+    if (smax < s_phys) { s_phys = smax; limited = true; }
   }
   // S5/S6: distance to the boundary along the straight line or helix
   int next;
@@ -261,6 +262,8 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
     return kAlive;
   }
   t.nav = (uint32_t)vol | (vac << 16);
+  // a step cut short by the step limit ends with its continuous loss only
+  if (limited) return kAlive;
   // S9 (deferred): the process is chosen with u1 over the fixed order
   const R xs = u1 * stot;
   proc = (S == 1) ? 1 : 2;

@@ -117,3 +117,40 @@ def test_straight_gamma_leaks_through_vacuum_barrel():
                     np.array([[0.0, 0.0, 1.0]]), np.array([0], np.uint32))
     r = o.transport(p)
     assert r["leaked"][0] == 100.0 and int(r["steps"][0]) == 1
+
+
+def test_a_step_cut_short_by_the_step_limit_does_not_interact():
+    """Stepping reading (C9): a discrete interaction happens only where the sampled
+    interaction length ends the step; a step cut short by the range-based limit
+    s_max = max(0.2 R, min(R, 1 mm)) or by a boundary only loses energy continuously.
+    e- of 3.9 T_c in bulk Pb with Moller ionisation alone: delta rays (at most T/2 < 2 T_c)
+    cannot ionise in turn, so the delta rays counted are the primaries' interactions. Along
+    the primary's interaction-free slowing-down steps s_k, with the cross section at each
+    pre-step energy, I = sum Sigma(T_k) s_k; the mean count per primary lies between
+    1 - exp(-I) (a first interaction) and I (an interaction only lowers the cross section).
+    Interacting at the end of every limited step would give about one per 1 mm step."""
+    g = w.Geometry(kind=0, n_layers=1, materials=[w.PB], sub_materials=[0], sub_thickness=[1000.0], half_xy=1e6)
+    o = oracle.Oracle(g)
+    Tc = o.cuts(0)[0]
+    T0 = 3.9 * Tc
+
+    def energy_at_range(R):
+        lo, hi = 1e-3, T0
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if o.interp(1, 1, 0, mid) < R else (lo, mid)
+        return 0.5 * (lo + hi)
+
+    I, T = 0.0, T0
+    while T > 2.0 * Tc:
+        R = o.interp(1, 1, 0, T)
+        s = R if R <= 1.0 else max(0.2 * R, 1.0)
+        I += o.interp(1, 2, 0, T) * s
+        if s >= R:
+            break
+        T = energy_at_range(R - s)
+    n = 4000
+    r = o.transport(w.electrons(n, T0), process_mask=oracle.P_EIONI)
+    mean = int(r["created"][1]) / n
+    sd = math.sqrt(I / n)
+    assert 1.0 - math.exp(-I) - 4 * sd <= mean <= I + 4 * sd, (mean, I)
