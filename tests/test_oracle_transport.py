@@ -154,3 +154,40 @@ def test_a_step_cut_short_by_the_step_limit_does_not_interact():
     mean = int(r["created"][1]) / n
     sd = math.sqrt(I / n)
     assert 1.0 - math.exp(-I) - 4 * sd <= mean <= I + 4 * sd, (mean, I)
+
+
+def test_fraction_of_positrons_annihilating_in_flight():
+    """Stepping reading (C9), with a process that ends the track: 10 MeV e+ in bulk Pb with
+    annihilation as the only discrete process (photons do not interact, so all of them
+    leave). The positron survives its k-th interaction-free slowing-down step s_k with
+    probability exp(-Sigma(T_k) s_k), Sigma at the pre-step energy, so it annihilates in flight
+    with probability 1 - exp(-I), I = sum Sigma(T_k) s_k; otherwise at rest, into two photons
+    of exactly m_e c^2 each."""
+    g = w.Geometry(kind=0, n_layers=1, materials=[w.PB], sub_materials=[0], sub_thickness=[1000.0], half_xy=1e6)
+    o = oracle.Oracle(g)
+    T0 = 10.0
+
+    def energy_at_range(R, hi):
+        lo = 1e-6
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if o.interp(2, 1, 0, mid) < R else (lo, mid)
+        return 0.5 * (lo + hi)
+
+    I, T = 0.0, T0
+    while T >= 1e-3:
+        R = o.interp(2, 1, 0, T)
+        s = R if R <= 1.0 else max(0.2 * R, 1.0)
+        I += o.interp(2, 4, 0, T) * s
+        if s >= R:
+            break
+        T = energy_at_range(R - s, T)
+    n = 4000
+    p = w.Primaries(np.full(n, -11, np.int32), np.full(n, T0), np.zeros((n, 3)), np.tile([0.0, 0.0, 1.0], (n, 1)),
+                    np.arange(n, dtype=np.uint32))
+    r = o.transport(p, process_mask=oracle.P_ANNIH, outgoing=4 * n)
+    photons = r["outgoing"][r["outgoing"][:, 1] == 22]
+    assert len(photons) == 2 * n
+    in_flight = np.count_nonzero(np.abs(photons[:, 2] - ME) > 1e-9) / 2 / n
+    want = 1.0 - math.exp(-I)
+    assert abs(in_flight - want) <= 4 * math.sqrt(want * (1 - want) / n), (in_flight, want)
