@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 from paper_2209_15445_gb300 import workloads as W
+from published import published
 
 ELEMENTS = {82: ("Pb", 207.2, 11.35, 823.0), 74: ("W", 183.84, 19.3, 727.0), 8: ("O", 15.999, 1.141, 95.0)}
 
@@ -32,13 +33,13 @@ def pbwo4():
 
 def test_pdg_radiation_length_of_lead_tungstate(pbwo4):
     x0_g_cm2 = 1.0 / pbwo4.inv_X0(0) / 10.0 * W.PBWO4.density
-    assert abs(x0_g_cm2 / 7.39 - 1.0) < 0.01, x0_g_cm2
+    assert abs(x0_g_cm2 / published("x0_PbWO4") - 1.0) < 0.01, x0_g_cm2
 
 
 def test_pdg_z_over_a_of_lead_tungstate():
     w = mass_fractions(W.PBWO4)
     zoa = sum(w[z] * z / a for z, a, _ in W.PBWO4.elements)
-    assert abs(zoa - 0.41315) < 2e-4
+    assert abs(zoa - published("ZoA_PbWO4")) < 2e-4
 
 
 def test_one_element_compound_is_the_element():

@@ -19,9 +19,10 @@ from scipy import stats
 
 import oracle
 from paper_2209_15445_gb300 import workloads as W
+from published import published
 
 ME = 0.51099895
-K_PDG = 0.307075  # MeV cm^2 / mol (PDG Table "Passage of particles through matter")
+K_PDG = published("K_bethe")  # MeV cm^2 / mol
 
 
 @pytest.fixture(scope="module")
