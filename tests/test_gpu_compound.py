@@ -22,7 +22,7 @@ def test_tables_and_cuts_of_lead_tungstate():
     for m in range(2):
         rc, tc, kc = A.adept_get_cuts(tr.h, m)
         otc, okc = o.cuts(m)
-        assert rc == 0 and tc == pytest.approx(otc, rel=1e-12) and kc == pytest.approx(okc, rel=1e-12)
+        assert rc == 0 and tc == pytest.approx(otc, rel=1e-12, abs=0) and kc == pytest.approx(okc, rel=1e-12, abs=0)
         for s, nt in ((0, 3), (1, 4), (2, 5)):
             for t in range(nt):
                 rc, g = A.adept_get_table(tr.h, s, t, m, 0)

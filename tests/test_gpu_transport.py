@@ -183,7 +183,7 @@ def test_primaries_outside_leak_immediately():
                     np.array([[500.0, 0, 10.0], [0, 0, -5.0]]), np.array([[0, 0, 1.0], [0, 0, 1.0]]),
                     np.array([0, 1], np.uint32))
     edep, meta = gpu_run(tr, p)
-    assert meta.leaked_MeV == pytest.approx(100.0 + 5.0 + 2 * ME, rel=1e-15)
+    assert meta.leaked_MeV == pytest.approx(100.0 + 5.0 + 2 * ME, rel=1e-15, abs=0)
     assert edep.sum() == 0.0
     tr.close()
 

@@ -54,7 +54,7 @@ def test_cuts_match(slab, slab_o):
         rc, tc, kc = A.adept_get_cuts(slab.h, m)
         assert rc == 0
         otc, okc = slab_o.cuts(m)
-        assert tc == pytest.approx(otc, rel=1e-12) and kc == pytest.approx(okc, rel=1e-12)
+        assert tc == pytest.approx(otc, rel=1e-12, abs=0) and kc == pytest.approx(okc, rel=1e-12, abs=0)
 
 
 TABLES = [(0, 3), (1, 4), (2, 5)]

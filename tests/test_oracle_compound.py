@@ -49,7 +49,7 @@ def test_one_element_compound_is_the_element():
     for sp, nt in ((0, 3), (1, 4), (2, 5)):
         for t in range(nt):
             np.testing.assert_allclose(b.table(sp, t, 0), a.table(sp, t, 0), rtol=1e-14, atol=0)
-    assert a.cuts(0) == pytest.approx(b.cuts(0), rel=1e-14)
+    assert a.cuts(0) == pytest.approx(b.cuts(0), rel=1e-14, abs=0)
 
 
 def elemental(z, density=1.0):
@@ -64,9 +64,9 @@ def test_mixture_rules(pbwo4, E):
     els = {z: elemental(z) for z in w}  # density 1 g/cm^3: values per g/cm^2
     for f in ("mu_compton", "mu_photo"):
         mix = sum(w[z] * getattr(els[z], f)(0, E) for z in w)
-        assert getattr(pbwo4, f)(0, E) / rho == pytest.approx(mix, rel=1e-12), f
+        assert getattr(pbwo4, f)(0, E) / rho == pytest.approx(mix, rel=1e-12, abs=0), f
     mix = sum(w[z] * els[z].inv_X0(0) for z in w)
-    assert pbwo4.inv_X0(0) / rho == pytest.approx(mix, rel=1e-12)
+    assert pbwo4.inv_X0(0) / rho == pytest.approx(mix, rel=1e-12, abs=0)
 
 
 def test_transport_in_the_papers_calorimeter():

@@ -109,7 +109,7 @@ def test_chord_sum(slab_oracle):
         p = p + s * u
         total += s
         vol = nx
-    assert total == pytest.approx(400.0 / c, rel=1e-12)
+    assert total == pytest.approx(400.0 / c, rel=1e-12, abs=0)
 
 
 def test_helix_radius_turn_and_sense():
@@ -124,7 +124,7 @@ def test_helix_radius_turn_and_sense():
     assert p1[1] > 0 and np.sign(np.cross(u, [0, 0, B])[1] * -1) > 0
     # quarter turn: displacement rho * sqrt(2), direction rotated by 90 degrees
     p1, u1 = oracle.helix_move(B, T, -1, 0.5 * math.pi * rho, p0, u)
-    assert np.linalg.norm(p1) == pytest.approx(rho * math.sqrt(2), rel=1e-12)
+    assert np.linalg.norm(p1) == pytest.approx(rho * math.sqrt(2), rel=1e-12, abs=0)
     assert np.allclose(u1, [0, 1, 0], atol=1e-12)
     # full turns with a z component: xy returns, z advances linearly, p_T conserved
     c = 0.3
@@ -132,7 +132,7 @@ def test_helix_radius_turn_and_sense():
     s_turn = 2 * math.pi * rho  # transverse radius rho*u_T, covered at rate u_T per unit path
     p1, u1 = oracle.helix_move(B, T, 1, 3 * s_turn, p0, u)
     assert np.allclose(p1[:2], 0.0, atol=1e-9 * rho)
-    assert p1[2] == pytest.approx(3 * s_turn * c, rel=1e-14)
+    assert p1[2] == pytest.approx(3 * s_turn * c, rel=1e-14, abs=0)
     assert np.allclose(u1, u, atol=1e-12)
     # many small steps equal one large step (the helix is exact)
     q = p0.copy(); v = u.copy()
@@ -140,7 +140,7 @@ def test_helix_radius_turn_and_sense():
         q, v = oracle.helix_move(B, T, 1, 10.0, q, v)
     p1, u1 = oracle.helix_move(B, T, 1, 1000.0, p0, u)
     assert np.allclose(q, p1, atol=1e-9) and np.allclose(v, u1, atol=1e-12)
-    assert math.hypot(v[0], v[1]) == pytest.approx(math.sqrt(1 - c * c), rel=1e-12)
+    assert math.hypot(v[0], v[1]) == pytest.approx(math.sqrt(1 - c * c), rel=1e-12, abs=0)
 
 
 def brute_helix_exit(o, T, q, B, p, u, vol, smax, h):

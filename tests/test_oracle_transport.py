@@ -107,7 +107,7 @@ def test_vacuum_looper_cap_barrel():
     p = w.Primaries(np.array([11], np.int32), np.array([5.0]), np.array([[100.0, 0.0, 0.0]]),
                     np.array([[0.0, 1.0, 0.0]]), np.array([0], np.uint32))
     r = o.transport(p, max_vacuum_steps=50)
-    assert r["killed"][0] == pytest.approx(5.0)
+    assert r["killed"][0] == pytest.approx(5.0, abs=0)
     assert int(r["steps"][1]) == 51
 
 
