@@ -214,8 +214,12 @@ typedef struct {
 
 /* Create a context: validates geometry and materials, lays out dev_arena (device memory
  * of arena_bytes owned by the caller, 256-byte aligned) for tables, track queues, event
- * slots and scoring. Returns ADEPT_ENOMEM if the arena cannot hold the minimum layout.
- * No device work yet beyond memory layout. */
+ * slots and scoring. Returns ADEPT_ENOMEM if the arena cannot hold the minimum layout,
+ * ADEPT_EINVAL (with adept_last_error) for invalid input, and writes *out only on
+ * success; the caller keeps ownership of every input array and of the arena, which must
+ * outlive the context. No device work yet beyond memory layout. Paper: the
+ * initialisation phase that sets up the geometry and materials once, kept apart from the
+ * run-time transport (Sec. 2.2), and the detector region handed to the GPU (Sec. 4). */
 int adept_init(adept_ctx** out, const adept_geometry* geometry, const adept_material* materials,
                int32_t n_materials, const adept_cuts* cuts, const adept_options* options,
                void* dev_arena, size_t arena_bytes, void* stream);

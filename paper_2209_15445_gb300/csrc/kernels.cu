@@ -14,7 +14,8 @@ namespace adept {
 enum { V_MUC, V_MUP, V_MUPH, V_SFULL, V_SE, V_IE, V_BE, V_SP, V_IP, V_BP, V_AP, V_RFULL, V_RE, V_RP, V_NROW };
 enum { B_RFULL, B_RE, B_RP };
 
-__device__ inline double node_E(int i) { return exp(kLnEmin + (double)i * kDlog); }
+using init::bin_integral;
+using init::node_E;
 
 __global__ void k_materials(const double* in, int n, MatDev* out) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -26,19 +27,6 @@ __device__ inline double s_full(const MatDev& M, double T) {
 }
 __device__ inline double s_restr(const MatDev& M, double T, double Tc, double kc, bool pos) {
   return init::dedx_col(M, T, Tc, pos) + init::dedx_rad(M, T, kc);
-}
-
-// Simpson rule with 8 panels of T/S(T) over bin i in ln T
-template <class F>
-__device__ inline double bin_integral(int i, F S) {
-  const double h = kDlog / 8.0;
-  double acc = 0.0;
-  for (int j = 0; j <= 8; ++j) {
-    const double T = exp(kLnEmin + (double)i * kDlog + (double)j * h);
-    const double w = (j == 0 || j == 8) ? 1.0 : ((j & 1) ? 4.0 : 2.0);
-    acc += w * (T / S(T));
-  }
-  return acc * h / 3.0;
 }
 
 __global__ void k_gamma_full(const MatDev* mats, int n_mat, BuildScratch s) {
@@ -57,19 +45,6 @@ __global__ void k_gamma_full(const MatDev* mats, int n_mat, BuildScratch s) {
     s.bins[((size_t)m * 3 + B_RFULL) * kNNode + i] = bin_integral(i, [&](double T) { return s_full(M, T); });
 }
 
-__device__ inline double clamp_cut(double x) { return x < 0.99e-3 ? 0.99e-3 : (x > 1e4 ? 1e4 : x); }
-
-// range of a stopping-power row: R(E0) = E0/(2 S(E0)) (S taken as 1/T below the grid),
-// then the running sum of the bin integrals
-__device__ inline void prefix_range(const double* S, const double* bins, double* R) {
-  double r = node_E(0) / (2.0 * S[0]);
-  R[0] = r;
-  for (int i = 0; i < kNNode - 1; ++i) {
-    r += bins[i];
-    R[i + 1] = r;
-  }
-}
-
 // production thresholds: e+- from the unrestricted range, gamma from 5 mean free paths
 __global__ void k_cuts(const MatDev* mats, int n_mat, double range_cut, BuildScratch s, double* Tc, double* kc) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,34 +52,10 @@ __global__ void k_cuts(const MatDev* mats, int n_mat, double range_cut, BuildScr
   if (mats[m].vacuum) { Tc[m] = 0.0; kc[m] = 0.0; return; }
   double* v = s.vals + (size_t)m * V_NROW * kNNode;
   double* Rf = v + V_RFULL * kNNode;
-  prefix_range(v + V_SFULL * kNNode, s.bins + ((size_t)m * 3 + B_RFULL) * kNNode, Rf);
-  double t_c = 1e6;
-  if (range_cut <= Rf[0]) {
-    t_c = node_E(0);
-  } else {
-    for (int i = 0; i < kNNode - 1; ++i)
-      if (Rf[i + 1] >= range_cut) {
-        const double t = (range_cut - Rf[i]) / (Rf[i + 1] - Rf[i]);
-        t_c = exp(kLnEmin + ((double)i + t) * kDlog);
-        break;
-      }
-  }
-  const double target = 5.0 / range_cut;
+  init::prefix_range(v + V_SFULL * kNNode, s.bins + ((size_t)m * 3 + B_RFULL) * kNNode, Rf);
   auto mu = [&](int i) { return v[V_MUC * kNNode + i] + v[V_MUP * kNNode + i] + v[V_MUPH * kNNode + i]; };
-  double k_c = 1e6;
-  if (mu(0) <= target) {
-    k_c = node_E(0);
-  } else {
-    for (int i = 0; i < kNNode - 1; ++i)
-      if (mu(i + 1) <= target) {
-        const double a = mu(i), b = mu(i + 1);
-        const double t = (a - target) / (a - b);
-        k_c = exp(kLnEmin + ((double)i + t) * kDlog);
-        break;
-      }
-  }
-  Tc[m] = clamp_cut(t_c);
-  kc[m] = clamp_cut(k_c);
+  Tc[m] = init::clamp_cut(init::range_threshold(Rf, range_cut));
+  kc[m] = init::clamp_cut(init::gamma_threshold(mu, range_cut));
 }
 
 __global__ void k_charged(const MatDev* mats, int n_mat, BuildScratch s, const double* Tc, const double* kc) {
@@ -135,7 +86,7 @@ __global__ void k_ranges(const MatDev* mats, int n_mat, BuildScratch s) {
   const int m = idx >> 1, pos = idx & 1;
   if (mats[m].vacuum) return;
   double* v = s.vals + (size_t)m * V_NROW * kNNode;
-  prefix_range(v + (pos ? V_SP : V_SE) * kNNode, s.bins + ((size_t)m * 3 + (pos ? B_RP : B_RE)) * kNNode,
+  init::prefix_range(v + (pos ? V_SP : V_SE) * kNNode, s.bins + ((size_t)m * 3 + (pos ? B_RP : B_RE)) * kNNode,
                v + (pos ? V_RP : V_RE) * kNNode);
 }
 

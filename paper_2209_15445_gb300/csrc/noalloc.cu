@@ -29,38 +29,6 @@ struct MatIn {
 
 enum { R_MUC, R_MUP, R_MUPH, R_SFULL, R_SE, R_IE, R_BE, R_SP, R_IP, R_BP, R_AP, R_RFULL, R_RE, R_RP, R_BFULL, R_BE_, R_BP_ };
 
-__device__ inline double nodeE(int i) { return exp(kLnEmin + (double)i * kDlog); }
-
-template <class F>
-__device__ inline double simpson_bin(int i, F S) {
-  const double h = kDlog / 8.0;
-  double acc = 0.0;
-  for (int j = 0; j <= 8; ++j) {
-    const double T = exp(kLnEmin + (double)i * kDlog + (double)j * h);
-    const double w = (j == 0 || j == 8) ? 1.0 : ((j & 1) ? 4.0 : 2.0);
-    acc += w * (T / S(T));
-  }
-  return acc * h / 3.0;
-}
-
-__device__ inline void running_range(const double* S, const double* bins, double* R) {
-  double r = nodeE(0) / (2.0 * S[0]);
-  R[0] = r;
-  for (int i = 0; i < kNNode - 1; ++i) {
-    r += bins[i];
-    R[i + 1] = r;
-  }
-}
-
-__device__ inline double invert_rising(const double* R, double target) {
-  if (target <= R[0]) return nodeE(0);
-  for (int i = 0; i < kNNode - 1; ++i)
-    if (R[i + 1] >= target) return exp(kLnEmin + ((double)i + (target - R[i]) / (R[i + 1] - R[i])) * kDlog);
-  return 1e6;
-}
-
-__device__ inline double clampc(double x) { return x < 0.99e-3 ? 0.99e-3 : (x > 1e4 ? 1e4 : x); }
-
 // one block per material; output tables [m][12][289] (gamma 3, e- 4, e+ 5) and cuts [m][2]
 __global__ void k_tables_noalloc(MatIn in, double range_cut, double* scratch, double* out, double* cuts) {
   const int m = blockIdx.x;
@@ -78,32 +46,19 @@ __global__ void k_tables_noalloc(MatIn in, double range_cut, double* scratch, do
   }
   auto full = [&](double T) { return init::dedx_col(M, T, T, false) + init::dedx_rad(M, T, T); };
   if (i < kNNode) {
-    const double E = nodeE(i);
+    const double E = init::node_E(i);
     w[R_MUC * kNNode + i] = init::mu_compton(M, E);
     w[R_MUP * kNNode + i] = init::mu_pair(M, E);
     w[R_MUPH * kNNode + i] = init::mu_photo(M, E);
     w[R_SFULL * kNNode + i] = full(E);
-    if (i < kNNode - 1) w[R_BFULL * kNNode + i] = simpson_bin(i, full);
+    if (i < kNNode - 1) w[R_BFULL * kNNode + i] = init::bin_integral(i, full);
   }
   __syncthreads();
   if (i == 0) {
-    running_range(w + R_SFULL * kNNode, w + R_BFULL * kNNode, w + R_RFULL * kNNode);
-    const double t_c = invert_rising(w + R_RFULL * kNNode, range_cut);
-    // gamma threshold: 5 mean free paths equal the cut on the falling low-energy branch
-    const double target = 5.0 / range_cut;
+    init::prefix_range(w + R_SFULL * kNNode, w + R_BFULL * kNNode, w + R_RFULL * kNNode);
     auto mu = [&](int k) { return w[R_MUC * kNNode + k] + w[R_MUP * kNNode + k] + w[R_MUPH * kNNode + k]; };
-    double k_c = 1e6;
-    if (mu(0) <= target) {
-      k_c = nodeE(0);
-    } else {
-      for (int k = 0; k < kNNode - 1; ++k)
-        if (mu(k + 1) <= target) {
-          k_c = exp(kLnEmin + ((double)k + (mu(k) - target) / (mu(k) - mu(k + 1))) * kDlog);
-          break;
-        }
-    }
-    tc = clampc(t_c);
-    kc = clampc(k_c);
+    tc = init::clamp_cut(init::range_threshold(w + R_RFULL * kNNode, range_cut));
+    kc = init::clamp_cut(init::gamma_threshold(mu, range_cut));
     cuts[2 * m] = tc;
     cuts[2 * m + 1] = kc;
   }
@@ -112,7 +67,7 @@ __global__ void k_tables_noalloc(MatIn in, double range_cut, double* scratch, do
   auto se = [&](double T) { return init::dedx_col(M, T, Tc, false) + init::dedx_rad(M, T, Kc); };
   auto sp = [&](double T) { return init::dedx_col(M, T, Tc, true) + init::dedx_rad(M, T, Kc); };
   if (i < kNNode) {
-    const double T = nodeE(i);
+    const double T = init::node_E(i);
     w[R_SE * kNNode + i] = se(T);
     w[R_IE * kNNode + i] = init::lambda_ioni(M, T, Tc, false);
     w[R_BE * kNNode + i] = init::lambda_brem(M, T, Kc);
@@ -121,13 +76,13 @@ __global__ void k_tables_noalloc(MatIn in, double range_cut, double* scratch, do
     w[R_BP * kNNode + i] = init::lambda_brem(M, T, Kc);
     w[R_AP * kNNode + i] = init::lambda_annih(M, T);
     if (i < kNNode - 1) {
-      w[R_BE_ * kNNode + i] = simpson_bin(i, se);
-      w[R_BP_ * kNNode + i] = simpson_bin(i, sp);
+      w[R_BE_ * kNNode + i] = init::bin_integral(i, se);
+      w[R_BP_ * kNNode + i] = init::bin_integral(i, sp);
     }
   }
   __syncthreads();
-  if (i == 0) running_range(w + R_SE * kNNode, w + R_BE_ * kNNode, w + R_RE * kNNode);
-  if (i == 1) running_range(w + R_SP * kNNode, w + R_BP_ * kNNode, w + R_RP * kNNode);
+  if (i == 0) init::prefix_range(w + R_SE * kNNode, w + R_BE_ * kNNode, w + R_RE * kNNode);
+  if (i == 1) init::prefix_range(w + R_SP * kNNode, w + R_BP_ * kNNode, w + R_RP * kNNode);
   __syncthreads();
   const int rows[12] = {R_MUC, R_MUP, R_MUPH, R_SE, R_RE, R_IE, R_BE, R_SP, R_RP, R_IP, R_BP, R_AP};
   if (i < kNNode)

@@ -8,24 +8,27 @@
 namespace adept {
 namespace init {
 
-// Klein-Nishina total cross section per electron [mm^2]. Below kappa = 0.02 its Taylor
-// series is used: the closed form cancels terms of size 1/kappa^2 down to O(1) there.
+// Klein-Nishina total cross section per electron [mm^2], 2 pi re^2 b(k). The closed form
+// of b cancels terms of size 1/k^2 down to O(1) (relative error about 1e-16/k^2 in FP64),
+// so below k = 0.2 b is taken from its Taylor series in x = 2k instead: term by term from
+// the expansions of ln(1+x), 1/(1+x) and 1/(1+x)^2, b = sum_n (-x)^n d_n with
+// d_n = 4(n+1)/(n+3) + 1/(n+1) - 2n/(n+2) + n/2 - 1 (d_0 = 4/3, Thomson), 60 terms.
+__device__ inline double kn_series_term(int n) {
+  const double dn = (double)n;
+  return 4.0 * (dn + 1.0) / (dn + 3.0) + 1.0 / (dn + 1.0) - 2.0 * dn / (dn + 2.0) + 0.5 * dn - 1.0;
+}
 __device__ inline double sigma_kn(double k) {
-  if (k >= 0.02) {
+  double b;
+  if (k >= 0.2) {
     const double l = log1p(2.0 * k);
     const double a = 1.0 + 2.0 * k;
-    const double b = (1.0 + k) / (k * k) * (2.0 * (1.0 + k) / a - l / k) + l / (2.0 * k) -
-                     (1.0 + 3.0 * k) / (a * a);
-    return 2.0 * kPi * kRe * kRe * b;
+    b = (1.0 + k) / (k * k) * (2.0 * (1.0 + k) / a - l / k) + l / (2.0 * k) - (1.0 + 3.0 * k) / (a * a);
+  } else {
+    const double mx = -2.0 * k;
+    b = kn_series_term(59);
+    for (int n = 58; n >= 0; --n) b = fma(b, mx, kn_series_term(n));
   }
-  // exact rational coefficients of the expansion in kappa (sigma / (2 pi re^2))
-  const double c[14] = {4.0 / 3.0,          -8.0 / 3.0,         104.0 / 15.0,     -266.0 / 15.0,
-                        4576.0 / 105.0,     -2176.0 / 21.0,     15136.0 / 63.0,   -24592.0 / 45.0,
-                        606208.0 / 495.0,   -447488.0 / 165.0,  2551808.0 / 429.0, -3533312.0 / 273.0,
-                        38182912.0 / 1365.0, -6311936.0 / 105.0};
-  double s = c[13];
-  for (int i = 12; i >= 0; --i) s = s * k + c[i];
-  return 2.0 * kPi * kRe * kRe * s;
+  return 2.0 * kPi * kRe * kRe * b;
 }
 
 // Tsai radiation length per atom (PDG): Lrad = ln(184.15 Z^-1/3), L'rad = ln(1194 Z^-2/3),
@@ -188,6 +191,66 @@ __device__ inline double lambda_annih(const MatDev& m, double T) {
   const double s2 = tau * (tau + 2.0), s = sqrt(s2);
   return m.n_el * kPi * kRe * kRe / (g + 1.0) *
          ((g * g + 4.0 * g + 1.0) / s2 * log1p(tau + s) - (g + 3.0) / s);
+}
+
+// ---------------------------------------------------------------- range and thresholds
+// Shared by the arena build (kernels.cu) and the allocation-free build (noalloc.cu), so
+// that both builds follow one set of rules.
+
+// energy of grid node i
+__device__ inline double node_E(int i) { return exp(kLnEmin + (double)i * kDlog); }
+
+// Simpson rule with 8 panels of T/S(T) over bin i in ln T: the range gained across bin i
+template <class F>
+__device__ inline double bin_integral(int i, F S) {
+  const double h = kDlog / 8.0;
+  double acc = 0.0;
+  for (int j = 0; j <= 8; ++j) {
+    const double T = exp(kLnEmin + (double)i * kDlog + (double)j * h);
+    const double w = (j == 0 || j == 8) ? 1.0 : ((j & 1) ? 4.0 : 2.0);
+    acc += w * (T / S(T));
+  }
+  return acc * h / 3.0;
+}
+
+// range of a stopping-power row: R(E0) = E0/(2 S(E0)) (S taken as 1/T below the grid),
+// then the running sum of the bin integrals
+__device__ inline void prefix_range(const double* S, const double* bins, double* R) {
+  double r = node_E(0) / (2.0 * S[0]);
+  R[0] = r;
+  for (int i = 0; i < kNNode - 1; ++i) {
+    r += bins[i];
+    R[i + 1] = r;
+  }
+}
+
+// production thresholds are clamped to [0.99 keV, 10 GeV]
+__device__ inline double clamp_cut(double x) { return x < 0.99e-3 ? 0.99e-3 : (x > 1e4 ? 1e4 : x); }
+
+// e+- threshold: the energy whose unrestricted range R (node values, rising) equals the
+// range cut, by exact inversion of the range interpolated linearly in ln E
+__device__ inline double range_threshold(const double* R, double range_cut) {
+  if (range_cut <= R[0]) return node_E(0);
+  for (int i = 0; i < kNNode - 1; ++i)
+    if (R[i + 1] >= range_cut) {
+      const double t = (range_cut - R[i]) / (R[i + 1] - R[i]);
+      return exp(kLnEmin + ((double)i + t) * kDlog);
+    }
+  return 1e6;
+}
+
+// gamma threshold: five mean free paths equal the range cut, on the falling low-energy
+// branch of the total attenuation mu(i) (node values)
+template <class F>
+__device__ inline double gamma_threshold(F mu, double range_cut) {
+  const double target = 5.0 / range_cut;
+  if (mu(0) <= target) return node_E(0);
+  for (int i = 0; i < kNNode - 1; ++i)
+    if (mu(i + 1) <= target) {
+      const double a = mu(i), b = mu(i + 1);
+      return exp(kLnEmin + ((double)i + (a - target) / (a - b)) * kDlog);
+    }
+  return 1e6;
 }
 
 }  // namespace init

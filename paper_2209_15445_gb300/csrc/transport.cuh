@@ -1,7 +1,7 @@
 // Device side of one transport step, shared by the per-species generation kernels
-// (kernels.cu) and the persistent multi-generation kernel (persistent.cu): track load and
-// store, phase A (S1-S8), phase B (S9), scoring (S10), warp-aggregated appends and the
-// per-warp ring of deferred interactions.
+// (kernels.cu, variants.cu) and the one-kernel-per-generation form (fused.cu): track load
+// and store, phase A (S1-S8), phase B (S9), scoring (S10), warp-aggregated appends and
+// the per-warp ring of deferred interactions.
 //
 // Queue descriptors are read from P.qd (device memory) with a runtime parity index:
 // indexing the kernel-parameter copy P.q that way makes the compiler copy the parameter

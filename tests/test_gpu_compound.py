@@ -67,5 +67,12 @@ def test_bad_compounds_rejected():
                        half_xy=100.0)
         with pytest.raises(A.AdeptError):
             make(g, precision=1)
-    # the allocation-free table build takes single elements only
-    assert A.adept_build_tables_noalloc([W.PBWO4], 0.7, 0, 0, None) == A.EINVAL
+    # the allocation-free table build takes single elements only: with valid output
+    # buffers, only the compound (alone, or after a valid element) makes it refuse
+    import torch
+    out = torch.zeros(2 * 12 * A.NNODE, dtype=torch.float64, device="cuda")
+    cuts = torch.zeros(4, dtype=torch.float64, device="cuda")
+    assert A.adept_build_tables_noalloc([W.PB], 0.7, out.data_ptr(), cuts.data_ptr(), None) == A.OK
+    assert A.adept_build_tables_noalloc([W.PBWO4], 0.7, out.data_ptr(), cuts.data_ptr(), None) == A.EINVAL
+    assert A.adept_build_tables_noalloc([W.PB, W.PBWO4], 0.7, out.data_ptr(), cuts.data_ptr(), None) == A.EINVAL
+    torch.cuda.synchronize()
