@@ -353,6 +353,7 @@ def run_ours(a):
                            "blocks_per_sm_species": list(tr.options.blocks_per_sm_species) if not a.bps else [a.bps] * 3,
                            "l2": "track queues (GBs) exceed L2; 256 MB buffer written between steps"},
                 "showers_per_s": showers, "steps_per_shower": steps / (a.steps * n),
+                "generations_per_step": (s1.generations - s0.generations) / a.steps,
                 "energy_conserved": bool(edep_ok), "roofline": roof, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

@@ -156,6 +156,14 @@ typedef struct {
   uint32_t max_outgoing;      /* outgoing particles kept between two status reads (a ring in the
                                  arena, 64 bytes each); more make adept_transport return
                                  ADEPT_ENOMEM [arena_bytes / 1024, within 2^16 .. 2^26] */
+  int32_t tail_tracks;        /* when fewer tracks than this, and than an eighth of the peak
+                                 since the queues were last empty, are live (at the last status,
+                                 plus an estimate for requests admitted since), the next chunk
+                                 runs as a tail chunk: one generation per iteration of a
+                                 conditional graph loop that stops as soon as the queues are
+                                 empty (no empty generations at the end of a transport), once
+                                 4 x tail_tracks are live, or after graph_generations
+                                 generations; < 0: never [16384] */
 } adept_options;
 
 /* adept_options.flags: time every generation (its three transport kernels, from the fork to

@@ -77,7 +77,8 @@ class adept_options(C.Structure):
                 ("blocks_per_sm_species", C.c_int32 * 3), ("fused", C.c_int32),
                 ("physics", C.c_uint32), ("msc_range_factor", C.c_double),
                 ("field_max_iterations", C.c_int32), ("delta_chord_mm", C.c_double),
-                ("delta_intersection_mm", C.c_double), ("max_outgoing", C.c_uint32)]
+                ("delta_intersection_mm", C.c_double), ("max_outgoing", C.c_uint32),
+                ("tail_tracks", C.c_int32)]
 
 
 TRACK_DTYPE = np.dtype([("pdg", "<i4"), ("pad0", "<i4"), ("E", "<f8"), ("pos", "<f8", 3), ("dir", "<f8", 3),

@@ -129,6 +129,17 @@ struct adept_ctx {
   int fgrid = 0, fminb = 0;  // fused generation kernel
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one per status buffer (own timing events)
   int graph_gens = 0;
+  // tail chunks (one per status buffer): a conditional while node runs one generation per
+  // iteration until the queues are empty, so the end of a transport launches no empty
+  // generations; chosen once the live tracks at the last status fall below kTailTracks
+  cudaGraphExec_t tgraph[2] = {nullptr, nullptr};
+  bool tail[2] = {false, false};  // the chunk queued in buffer b is a tail chunk
+  uint64_t last_live = 0;         // live tracks at the end of the last chunk read back
+  uint64_t peak_live = 0;         // most live tracks seen since the queues were last empty
+  // estimated peak tracks (tracks_per_MeV x energy, plus the primaries) of the requests
+  // admitted so far; its value when chunk b was launched; and the value behind last_live
+  uint64_t admit_est = 0, admit_mark[2] = {0, 0}, admit_seen = 0;
+  cudaStream_t bstream = nullptr; // captures the tail chunks' loop body
   std::vector<cudaEvent_t> ev;  // 4 per generation when timing: start, after e-, after e+, after gamma
   cudaStream_t side[2] = {nullptr, nullptr};     // the e+ and gamma kernels run on these
   cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
@@ -312,6 +323,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (o.block_size < 32 || o.block_size > 256 || (o.block_size & 31)) return ADEPT_EINVAL;
   if (o.graph_generations < -1 || o.graph_generations > 1024) return ADEPT_EINVAL;
   if (o.graph_generations == 0) o.graph_generations = 32;
+  if (o.tail_tracks == 0) o.tail_tracks = 16384;
   if (o.seed == 0) o.seed = 1;
   if (o.max_steps == 0) o.max_steps = 100000;
   if (o.max_vacuum_steps == 0) o.max_vacuum_steps = 1000;
@@ -397,6 +409,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   P.chord_iter = o.field_max_iterations;
   P.delta_chord = o.delta_chord_mm;
   P.delta_int = o.delta_intersection_mm;
+  P.tail_exit = o.tail_tracks > 0 ? (uint32_t)std::min<uint64_t>(4ull * (uint64_t)o.tail_tracks, 0xFFFFFFFFull) : 0u;
   c->steplen = steplen;
   // device state
   adept_ctx* c_ = cp;
@@ -424,6 +437,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     }
     CK(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     CK(cudaStreamCreateWithFlags(&c->tstream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->bstream, cudaStreamNonBlocking));
     for (int j = 0; j < 3; ++j) CK(cudaEventCreateWithFlags(&c->kdone[j], cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&c->tjoin, cudaEventDisableTiming));
     CK(cudaStreamSynchronize(c->stream));
@@ -596,6 +610,7 @@ static int admit(adept_ctx* c) {
       for (uint32_t k = 0; k < r->remaining; ++k) c->slot_req[base + k] = r->id;
       c->energy_in_flight += r->energy;
       c->in_flight++;
+      c->admit_est += (uint64_t)(r->energy * c->opt.tracks_per_MeV) + r->n;
     }
     const size_t nk = r->keys.size();
     // pinned staging: tracks (host submissions), meta, keys
@@ -688,6 +703,78 @@ static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b, bool captu
   return e;
 }
 
+// Below adept_options.tail_tracks live tracks a generation is dominated by its launch, and
+// a tail chunk trades the programmatic launch between generations (about 5 us a generation
+// on GB300) for stopping exactly when the last track dies (a fixed chunk runs to its end and
+// one more is queued behind it, both empty at the end of a transport). So tail chunks are
+// kept for the decay at the end: fewer live tracks than tail_tracks and than a kTailDecay-th
+// of the peak since the queues were last empty. A tail chunk runs at most
+// graph_generations generations, like a fixed one, so the status is read as often.
+constexpr uint64_t kTailDecay = 8;
+
+// A tail chunk: open (condition = live tracks) -> while (condition) { one generation (the
+// three species kernels, or the fused kernel) -> step (++tail_k, condition = live tracks,
+// fewer than 4 tail_tracks, and tail_k < graph_generations) } -> end of chunk with the count
+// the loop left. No timing records (event nodes are not allowed in a conditional body).
+static int capture_tail_graph(adept_ctx* c, int b) {
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(c, ADEPT_ECUDA, "tail capture: %s", cudaGetErrorString(e));
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  e = cudaMemsetAsync(&c->P.ctrl->done_count[b], 0, sizeof(uint32_t), c->stream);
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = launch_tail_open(c->P, h, c->stream);
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, &deps, nullptr, &ndeps);
+  cudaGraphNode_t loop = nullptr;
+  cudaGraph_t body = nullptr;
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&loop, g, deps, nullptr, ndeps, &cp);
+    if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+  }
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(c->stream, &loop, nullptr, 1, cudaStreamSetCaptureDependencies);
+  // the loop body: one generation, captured on a stream of its own
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(c->bstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaStream_t s0 = c->bstream;
+    if (c->opt.fused) {
+      e = launch_fused_generation(c->P, kGkDevice, c->opt.precision, c->fminb, c->fgrid, c->block, false, s0);
+    } else {
+      e = cudaEventRecord(c->fork, s0);
+      for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->side[j], c->fork, 0);
+      cudaStream_t st[3] = {c->side[1], s0, c->side[0]};  // gamma, e-, e+
+      for (int sp : {1, 2, 0})
+        if (e == cudaSuccess) e = launch_transport(c->P, kGkDevice, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, false, st[sp]);
+      for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventRecord(c->join[j], c->side[j]);
+      for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(s0, c->join[j], 0);
+    }
+    if (e == cudaSuccess) e = launch_tail_step(c->P, h, (uint32_t)c->opt.graph_generations, s0);
+    cudaGraph_t bg = nullptr;
+    const cudaError_t e3 = cudaStreamEndCapture(s0, &bg);
+    if (e == cudaSuccess) e = e3;
+  }
+  if (e == cudaSuccess) e = launch_finish(c->P, b, kGkDevice, c->stream);
+  cudaGraph_t out = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(c->stream, &out);
+  if (e != cudaSuccess) {
+    if (out) cudaGraphDestroy(out);
+    return fail(c, ADEPT_ECUDA, "tail graph capture: %s", cudaGetErrorString(e));
+  }
+  if (e2 != cudaSuccess) return fail(c, ADEPT_ECUDA, "tail graph capture end: %s", cudaGetErrorString(e2));
+  e = cudaGraphInstantiate(&c->tgraph[b], out, 0);
+  cudaGraphDestroy(out);
+  if (e != cudaSuccess) return fail(c, ADEPT_ECUDA, "tail graph instantiate: %s", cudaGetErrorString(e));
+  return ADEPT_OK;
+}
+
 static int capture_graph(adept_ctx* c, int gens, int b) {
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
@@ -714,16 +801,28 @@ static int launch_chunk(adept_ctx* c, int b) {
     int rc = ensure_events(c, 8 * gens);
     if (rc) return rc;
   }
-  if (G > 0) {
+  const uint64_t live = c->last_live + (c->admit_est - c->admit_seen);
+  c->tail[b] = G > 0 && c->opt.tail_tracks > 0 && live < (uint64_t)c->opt.tail_tracks &&
+               live * kTailDecay < c->peak_live;
+  c->admit_mark[b] = c->admit_est;
+  if (c->tail[b]) {
+    if (!c->tgraph[b]) {
+      int rc = capture_tail_graph(c, b);
+      if (rc) return rc;
+    }
+    CK(cudaGraphLaunch(c->tgraph[b], c->stream));
+    c->stats.launches += 4;  // open, end of chunk, mark, finish; the loop's kernels once read back
+  } else if (G > 0) {
     if (!c->graph[b]) {
       int rc = capture_graph(c, G, b);
       if (rc) return rc;
     }
     CK(cudaGraphLaunch(c->graph[b], c->stream));
+    c->stats.launches += (c->opt.fused ? 1 : 3) * gens + 3;
   } else {
     CK(enqueue_generations(c, 1, b, false));
+    c->stats.launches += (c->opt.fused ? 1 : 3) * gens + 3;
   }
-  c->stats.launches += (c->opt.fused ? 1 : 3) * gens + 3;
   CK(cudaMemcpyAsync(c->h_ctrl[b], c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(c->h_done[b], c->P.evt.done_list[b], sizeof(uint32_t) * kDoneChunk, cudaMemcpyDeviceToHost,
                      c->stream));
@@ -734,6 +833,10 @@ static int launch_chunk(adept_ctx* c, int b) {
 // Wait for chunk b and account its timing events.
 static int wait_chunk(adept_ctx* c, int b) {
   CK(cudaEventSynchronize(c->status_ev[b]));
+  if (c->tail[b]) {  // the loop's generations: the species kernels (or the fused one) and a step kernel
+    c->stats.launches += (uint64_t)c->h_ctrl[b]->tail_k * ((c->opt.fused ? 1 : 3) + 1);
+    return ADEPT_OK;
+  }
   if (timing(c)) {
     const int G = c->opt.graph_generations;
     const int gens = G > 0 ? G : 1;
@@ -896,6 +999,9 @@ extern "C" int adept_transport(adept_ctx* c, uint64_t timeout_us) {
       }
     }
     const uint32_t live = h.count[h.gen % 3][0].n + h.count[h.gen % 3][1].n + h.count[h.gen % 3][2].n;
+    c->last_live = live;
+    c->admit_seen = c->admit_mark[b];
+    c->peak_live = live ? std::max<uint64_t>(c->peak_live, live) : 0;
     idle_chunks = (live == 0 && done.empty()) ? idle_chunks + 1 : 0;
     if (idle_chunks > 8) {
       std::lock_guard<std::mutex> lk(c->mu);
@@ -1238,8 +1344,10 @@ extern "C" const char* adept_last_error(const adept_ctx* c) {
 extern "C" void adept_destroy(adept_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < 2; ++b) {
     if (c->graph[b]) cudaGraphExecDestroy(c->graph[b]);
+    if (c->tgraph[b]) cudaGraphExecDestroy(c->tgraph[b]);
+  }
   for (auto e : c->ev) cudaEventDestroy(e);
   for (int j = 0; j < 2; ++j) {
     if (c->side[j]) { cudaStreamSynchronize(c->side[j]); cudaStreamDestroy(c->side[j]); }
@@ -1248,6 +1356,7 @@ extern "C" void adept_destroy(adept_ctx* c) {
   if (c->submit_stream) { cudaStreamSynchronize(c->submit_stream); cudaStreamDestroy(c->submit_stream); }
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->tstream) { cudaStreamSynchronize(c->tstream); cudaStreamDestroy(c->tstream); }
+  if (c->bstream) cudaStreamDestroy(c->bstream);
   for (int j = 0; j < 3; ++j)
     if (c->kdone[j]) cudaEventDestroy(c->kdone[j]);
   if (c->tjoin) cudaEventDestroy(c->tjoin);

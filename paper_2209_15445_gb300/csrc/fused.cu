@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(256, MINB) k_fused_generation(Params P, uint32
   WarpRing<R>& ring = rings[threadIdx.x >> 5];
   grid_dependency_wait();
   allow_dependent_launch();
+  if (gk == kGkDevice) gk = __ldcg(&P.ctrl->tail_k);  // a generation of a tail chunk
   const uint32_t gen = __ldcg(&P.ctrl->gen) + gk;
   if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) open_generation(P, gen, gk);

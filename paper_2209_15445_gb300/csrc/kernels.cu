@@ -253,6 +253,8 @@ cudaError_t launch_init_primaries(const Params& P, const TrackIn* recs, const ui
 __global__ void k_end_chunk(Params P, uint32_t gens) {
   if (threadIdx.x != 0) return;
   volatile Ctrl* c = P.ctrl;
+  if (gens == kGkDevice) gens = c->tail_k;
+  if (gens == 0) return;  // a tail chunk that found the queues empty ran nothing
   const uint32_t gen = c->gen + gens;
   const uint32_t ln = c->log_n;
   if (ln < P.max_log) {
@@ -292,8 +294,36 @@ __global__ void k_finish(Params P, int b) {
   }
 }
 
-cudaError_t launch_finish(const Params& P, int b, int gens, cudaStream_t st) {
-  k_end_chunk<<<1, 32, 0, st>>>(P, (uint32_t)gens);
+// Tail chunks (conditional while node): the condition that runs the next generation. Live
+// tracks are the sizes of the generation slot the next generation reads.
+__device__ __forceinline__ uint32_t live_tracks(const Params& P, uint32_t gen) {
+  const uint32_t cr = gen % 3;
+  return min(__ldcg(&P.ctrl->count[cr][0].n), P.cap) + min(__ldcg(&P.ctrl->count[cr][1].n), P.cap) +
+         min(__ldcg(&P.ctrl->count[cr][2].n), P.cap);
+}
+__global__ void k_tail_open(Params P, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  P.ctrl->tail_k = 0;
+  cudaGraphSetConditional(h, live_tracks(P, __ldcg(&P.ctrl->gen)) > 0 ? 1u : 0u);
+}
+__global__ void k_tail_step(Params P, cudaGraphConditionalHandle h, uint32_t max_gens) {
+  if (threadIdx.x != 0) return;
+  const uint32_t k = __ldcg(&P.ctrl->tail_k) + 1;
+  P.ctrl->tail_k = k;
+  const uint32_t live = live_tracks(P, __ldcg(&P.ctrl->gen) + k);
+  cudaGraphSetConditional(h, (k < max_gens && live > 0 && live < P.tail_exit) ? 1u : 0u);
+}
+cudaError_t launch_tail_open(const Params& P, cudaGraphConditionalHandle h, cudaStream_t st) {
+  k_tail_open<<<1, 32, 0, st>>>(P, h);
+  return cudaGetLastError();
+}
+cudaError_t launch_tail_step(const Params& P, cudaGraphConditionalHandle h, uint32_t max_gens, cudaStream_t st) {
+  k_tail_step<<<1, 32, 0, st>>>(P, h, max_gens);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const Params& P, int b, uint32_t gens, cudaStream_t st) {
+  k_end_chunk<<<1, 32, 0, st>>>(P, gens);
   k_mark<<<1216, 256, 0, st>>>(P);
   k_finish<<<(P.evt.max_slots + 255) / 256 < 1216 ? (P.evt.max_slots + 255) / 256 : 1216, 256, 0, st>>>(P, b);
   return cudaGetLastError();

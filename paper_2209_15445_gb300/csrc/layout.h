@@ -89,7 +89,8 @@ struct Ctrl {
   uint32_t done_count[2];     // events found finished by the finish pass of a chunk (per buffer)
   uint32_t log_n;             // rows written to the generation log
   uint32_t error;             // first device-detected error code (0 = none)
-  uint32_t pad[4];
+  uint32_t tail_k;            // generations a tail chunk has run so far (see kGkDevice)
+  uint32_t pad[3];
   unsigned long long steps[3];
   unsigned long long created[3];
   unsigned long long overflow;
@@ -142,6 +143,7 @@ struct Params {
   int chord_iter;       // 0: analytic helix; N > 0: chord propagation capped at N iterations
   double delta_chord;   // chord sagitta limit, mm
   double delta_int;     // intersection accuracy, mm
+  uint32_t tail_exit;   // a tail chunk ends once this many tracks are live
 };
 
 // device view of one submitted particle; same layout as adept_track in adept.h
@@ -164,6 +166,10 @@ cudaError_t launch_build_tables(const Params& P, const double* mat_in, int n_mat
                                 MatDev* mat, BuildScratch s, double2* g64, double2* e64, double2* p64,
                                 float2* g32, float2* e32, float2* p32, double* re64, double* rp64,
                                 float* re32, float* rp32, double* Tc, double* kc, cudaStream_t st);
+// A tail chunk runs its generations as the body of a conditional (while) graph node, one
+// generation per iteration, until the queues are empty or a cap is reached; its kernels are
+// launched with gk = kGkDevice and read their place in the chunk from Ctrl::tail_k.
+constexpr uint32_t kGkDevice = 0xFFFFFFFFu;
 // generation gen + gk of one species (gk: its place in the chunk; the three species of a
 // generation may run concurrently). pdl: launch with a programmatic dependency on the
 // stream's preceding kernels (the previous generation's), see grid_dependency_wait.
@@ -174,8 +180,13 @@ cudaError_t launch_admit(const Params& P, uint32_t slot_base, const uint32_t* ke
 // meta: per track (event index within the request, track id)
 cudaError_t launch_init_primaries(const Params& P, const TrackIn* recs, const uint32_t* meta, int n,
                                   uint32_t slot_base, int precision, cudaStream_t st);
-// end of a chunk of `gens` generations: log the last one, advance gen, find finished events
-cudaError_t launch_finish(const Params& P, int buffer, int gens, cudaStream_t st);
+// end of a chunk of `gens` generations (kGkDevice: the count a tail chunk left in
+// Ctrl::tail_k): log the last one, advance gen, find finished events
+cudaError_t launch_finish(const Params& P, int buffer, uint32_t gens, cudaStream_t st);
+// tail chunks: before the loop, tail_k = 0 and the condition = live tracks in the queues;
+// after each generation, ++tail_k and the condition = live tracks and tail_k < max_gens
+cudaError_t launch_tail_open(const Params& P, cudaGraphConditionalHandle h, cudaStream_t st);
+cudaError_t launch_tail_step(const Params& P, cudaGraphConditionalHandle h, uint32_t max_gens, cudaStream_t st);
 cudaError_t launch_probe_philox(const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out,
                                 cudaStream_t st);
 cudaError_t launch_probe_interp(const Params& P, int s, int t, int m, int prec, const double* E, int n,

@@ -92,14 +92,40 @@ def test_generation_counts_across_chunk_lengths(chunk, fused):
     """Generation g reads its queue sizes from slot g mod 3 and its tracks from buffer g mod 2,
     and its place in the chunk comes in as an argument, so chunk lengths that are not
     multiples of 6 start the chunks at every phase of both. The sizes per generation must
-    still equal the oracle's exactly (FP64), in both the concurrent and the fused mode."""
+    still equal the oracle's exactly (FP64), in both the concurrent and the fused mode.
+    Tail chunks are off here, so that every chunk has the fixed length."""
     need_gpu()
     geom = W.slab_calorimeter()
     kw = dict(fused=1, blocks_per_sm=2) if fused else {}
-    tr = make(geom, precision=0, graph_generations=chunk, tuned=False, **kw)
+    tr = make(geom, precision=0, graph_generations=chunk, tuned=False, tail_tracks=-1, **kw)
     prim = W.mixed(4, seed=23)
     prim.E[:] = np.minimum(prim.E, 1000.0)
     compare_generations(tr, oracle.Oracle(geom), prim, 0)
+    tr.close()
+
+
+@pytest.mark.parametrize("fused,tail", [(0, 1 << 30), (1, 1 << 30), (0, 300)])
+def test_tail_chunks_stop_with_the_last_track(fused, tail):
+    """Tail chunks run one generation per iteration of a conditional graph loop and read
+    their place in the chunk from the device: the queue sizes per generation still equal the
+    oracle's exactly (FP64), and the transport runs exactly as many generations as the
+    oracle's showers last, with at most a few empty generations at the end: tail chunks take
+    over once the population has decayed below tail_tracks and an eighth of its peak, and a
+    fixed chunk of 8 is queued only while the status two chunks back was above both, so no
+    more than the rest of one fixed chunk and one more run past the last track."""
+    need_gpu()
+    geom = W.slab_calorimeter()
+    kw = dict(fused=1, blocks_per_sm=2) if fused else {}
+    tr = make(geom, precision=0, graph_generations=8, tuned=False, tail_tracks=tail, **kw)
+    prim = W.mixed(4, seed=23)
+    prim.E[:] = np.minimum(prim.E, 1000.0)
+    orc = oracle.Oracle(geom)
+    g0 = tr.stats().generations
+    compare_generations(tr, orc, prim, 0)
+    ran = tr.stats().generations - g0
+    ref = orc.transport(prim, max_gen=20000)["gen_hist"]
+    lasting = int(np.nonzero(ref.sum(axis=1))[0].max()) + 1  # generations with live tracks
+    assert lasting <= ran < lasting + 16, (ran, lasting)
     tr.close()
 
 
