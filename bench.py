@@ -68,6 +68,9 @@ def args_parse():
     ap.add_argument("--graph", type=int, default=0, help="generations per CUDA graph (0 = tuned)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form on the same workload")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--arena-gb", type=float, default=10.0)
     ap.add_argument("--bps", type=int, default=0, help="transport-kernel blocks/SM variant (0 = library default)")
     ap.add_argument("--bps-species", type=str, default="", help="per-species variants gamma,e-,e+")
@@ -335,6 +338,51 @@ def run_ours(a):
                "d2h_bytes_per_step": int(n * (geom.n_bins + 2) * 8), "steps": k2,
                "showers_per_s": ws * n * k2 / dt}
 
+    # the plain FP64 form on the same workload and GPU, in the same process (the comparison
+    # the split form is built for): FP64 physics, one array per field, its own tuned launch
+    fp64 = None
+    topt = tr.options
+    if a.precision and not a.no_fp64:
+        tr.close()
+        tr = None
+        del dev_tracks
+        torch.cuda.empty_cache()
+        dev64 = torch.from_numpy(host.view(np.uint8).copy()).to(dev)
+        t64 = A.Transport(geom, precision=0, arena_bytes=int(a.arena_gb * (1 << 30)), flags=A.FLAG_TIME_STEPS,
+                          max_events=max(65536, n))
+
+        def step64():
+            rid = t64.submit_device(dev64, n)
+            t64.transport()
+            return t64.result(rid, n)[1]
+
+        for _ in range(a.fp64_warmup):
+            step64()
+        f0 = t64.stats()
+        barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.fp64_steps)]
+        for k in range(a.fp64_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            evs[k][0].record(t64.stream)
+            m64 = step64()
+            evs[k][1].record(t64.stream)
+        barrier()
+        f1 = t64.stats()
+        ms64 = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+        st64 = sum(f1.steps) - sum(f0.steps)
+        km64 = f1.step_kernel_ms - f0.step_kernel_ms
+        ok64 = abs(m64.deposited_MeV + m64.leaked_MeV + m64.killed_MeV - n * E) <= 1e-9 * n * E
+        fp64 = {"value": st64 / (ms64 / 1e3), "unit": UNIT, "showers_per_s": n * a.fp64_steps / (ms64 / 1e3),
+                "ms_per_step": ms64 / a.fp64_steps, "steps": a.fp64_steps, "warmup": a.fp64_warmup,
+                "steps_per_shower": st64 / (a.fp64_steps * n), "energy_conserved": bool(ok64),
+                "blocks_per_sm_species": list(t64.options.blocks_per_sm_species),
+                "kernel_share_of_step_time": km64 / ms64 if ms64 else None,
+                "algorithmic_GBs": 76 * (2 * st64 - a.fp64_steps * n) / (km64 / 1e3) / 1e9 if km64 else None,
+                "split_over_fp64": value / (st64 / (ms64 / 1e3))}
+        t64.close()
+        del dev64
+
     base = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         base = cpu_baseline(E, physics=a.physics)
@@ -344,20 +392,21 @@ def run_ours(a):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32/f64" if a.precision else "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "events": n, "E_MeV": E, "precision": "split" if a.precision else "fp64",
-                           "graph_generations": tr.options.graph_generations,
-                           "block": tr.options.block_size or 256,
-                           "fused": int(tr.options.fused),
+                           "graph_generations": topt.graph_generations,
+                           "block": topt.block_size or 256,
+                           "fused": int(topt.fused),
                            "physics": {0: "paper process list", 1: "+ multiple scattering", 2: "+ loss fluctuations",
                                        3: "+ multiple scattering + loss fluctuations"}[a.physics],
-                           "blocks_per_sm": int(tr.options.blocks_per_sm),
-                           "blocks_per_sm_species": list(tr.options.blocks_per_sm_species) if not a.bps else [a.bps] * 3,
+                           "blocks_per_sm": int(topt.blocks_per_sm),
+                           "blocks_per_sm_species": list(topt.blocks_per_sm_species) if not a.bps else [a.bps] * 3,
                            "l2": "track queues (GBs) exceed L2; 256 MB buffer written between steps"},
                 "showers_per_s": showers, "steps_per_shower": steps / (a.steps * n),
                 "generations_per_step": (s1.generations - s0.generations) / a.steps,
-                "energy_conserved": bool(edep_ok), "roofline": roof, "cpu_baseline": base, "e2e": e2e,
+                "energy_conserved": bool(edep_ok), "roofline": roof, "fp64_form": fp64, "cpu_baseline": base, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
-    tr.close()
+    if tr is not None:
+        tr.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
