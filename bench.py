@@ -44,8 +44,8 @@ TRACK_BYTES_SPLIT = 64  # x,y,z f64 + direction 3 f32 + E f64 + id u64 + event, 
 # the ncu captures of generation 60 (profiles/transport_kernels_10gev_e_showers_gen60_full.md
 # for the split form, profiles/transport_kernels_10gev_e_showers_fp64_gen60_full.md for the
 # plain FP64 form); valid while the kernel sources hash to NCU_SRC_HASH, null otherwise
-NCU_BYTES_PER_STEP = {1: 112.4, 0: 136.8}
-NCU_SRC_HASH = "087a9c3e8e8c72cb"
+NCU_BYTES_PER_STEP = {1: 108.6, 0: 133.0}
+NCU_SRC_HASH = "3420490cf4d4cdc1"
 
 
 def kernel_src_hash() -> str:
@@ -372,6 +372,7 @@ def run_ours(a):
         ms64 = sum(e0.elapsed_time(e1) for e0, e1 in evs)
         st64 = sum(f1.steps) - sum(f0.steps)
         km64 = f1.step_kernel_ms - f0.step_kernel_ms
+        kn64 = f1.step_launches - f0.step_launches
         ok64 = abs(m64.deposited_MeV + m64.leaked_MeV + m64.killed_MeV - n * E) <= 1e-9 * n * E
         fp64 = {"value": st64 / (ms64 / 1e3), "unit": UNIT, "showers_per_s": n * a.fp64_steps / (ms64 / 1e3),
                 "ms_per_step": ms64 / a.fp64_steps, "steps": a.fp64_steps, "warmup": a.fp64_warmup,
@@ -379,6 +380,9 @@ def run_ours(a):
                 "blocks_per_sm_species": list(t64.options.blocks_per_sm_species),
                 "kernel_share_of_step_time": km64 / ms64 if ms64 else None,
                 "algorithmic_GBs": 76 * (2 * st64 - a.fp64_steps * n) / (km64 / 1e3) / 1e9 if km64 else None,
+                "mean_launch_us": 1e3 * km64 / kn64 if kn64 else None,
+                "traffic": (NCU_BYTES_PER_STEP[0] * st64 / kn64
+                            if kn64 and NCU_SRC_HASH == kernel_src_hash() else None),
                 "split_over_fp64": value / (st64 / (ms64 / 1e3))}
         t64.close()
         del dev64
