@@ -114,7 +114,8 @@ enum Outcome { kDead = 0, kAlive = 1, kInteract = 2 };
 // dep_bin. A positron that stops also returns kInteract (process 3): its annihilation at
 // rest runs with the interactions, from the same random stream, so that phase A emits no
 // secondaries (its appends take the one-ballot path, and the e+ kernel needs fewer
-// registers: 3 blocks per SM measured +2.4 % over 2). The variant V compiles
+// registers: 3 blocks per SM measured +2.4 % over 2). So does a track that leaves the world
+// (process 4), recorded there with its exit state (+0.9 %). The variant V compiles
 // in the optional parts, kept out of the kernels that do not use them: bit 0 the chord
 // propagator of the field (P.chord_iter > 0), bit 1 multiple scattering and loss
 // fluctuations (P.physics).
@@ -256,11 +257,7 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
   }
   // S8: boundary crossing
   if (boundary) {
-    if (next < 0) {
-      atomicAdd(P.evt.leaked + t.ev, t.E + rest);
-      record_leak(P, S == 0 ? 22 : (S == 1 ? 11 : -11), t.ev, t.E, t.x, t.y, t.z, t.u[0], t.u[1], t.u[2]);
-      return kDead;
-    }
+    if (next < 0) { proc = 4; return kInteract; }  // recorded as it leaves, in phase B
     t.nav = (uint32_t)next | (vac << 16);
     return kAlive;
   }
@@ -275,14 +272,23 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
   return kInteract;
 }
 
-// Phase B: the discrete interaction (S9) of a track queued by phase A, or the annihilation
-// at rest of a positron that stopped (process 3). Its random stream is rebuilt from (event,
+// Phase B: the discrete interaction (S9) of a track queued by phase A, the annihilation at
+// rest of a positron that stopped (process 3), or the outgoing record of a track that left
+// the world (process 4). Its random stream is rebuilt from (event,
 // id, step): block 0 was consumed in phase A, the models draw from block 1 on. Returns
 // whether the parent survives (with its new state in t).
 template <class R, int S>
 __device__ __forceinline__ bool step_interact(const Params& P, Trk<R>& t, uint32_t pstep, int proc, Ixn<R>& sec,
                                               double& dep) {
   Stream<R> rs(P.seed, __ldg(P.evt.key + t.ev), t.id, pstep);
+  if (proc == 4) {  // the track left the world: its energy and its outgoing record
+    sec.happened = false;
+    sec.n = 0;
+    dep = 0.0;
+    atomicAdd(P.evt.leaked + t.ev, t.E + (S == 2 ? 2.0 * kMe : 0.0));
+    record_leak(P, S == 0 ? 22 : (S == 1 ? 11 : -11), t.ev, t.E, t.x, t.y, t.z, t.u[0], t.u[1], t.u[2]);
+    return false;
+  }
   if (S == 2 && proc == 3) {  // a positron that stopped: two photons, drawn from block 1 on
     sec.happened = false;
     dep = 0.0;
