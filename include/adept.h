@@ -171,7 +171,9 @@ typedef struct {
 #define ADEPT_FLAG_TIME_STEPS 1
 /* also time each species kernel separately (two more events per generation) */
 #define ADEPT_FLAG_TIME_SPECIES 4
-/* histogram the length of every step (validation; costs one atomic per step) */
+/* histogram the length of every step (validation; costs one atomic per step; runs kernels
+ * compiled with the histogram, so not with fused = 1 or field_max_iterations > 0, which
+ * adept_init refuses with ADEPT_EINVAL) */
 #define ADEPT_FLAG_STEP_HISTOGRAM 8
 
 /* One particle handed to the library. event is the caller's event number; it keys the

@@ -313,8 +313,10 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   if (o.msc_range_factor < 0.0 || !(o.msc_range_factor < 1e30)) return ADEPT_EINVAL;
   if (o.msc_range_factor == 0.0) o.msc_range_factor = 0.04;
   if (o.field_max_iterations < 0) return ADEPT_EINVAL;
-  // the fused kernel has no variant with chords or the optional physics
+  // the fused kernel has no variant with chords, the optional physics or the step-length
+  // histogram, and the histogram is not compiled together with chords
   if (o.fused && (o.field_max_iterations > 0 || o.physics)) return ADEPT_EINVAL;
+  if ((o.flags & ADEPT_FLAG_STEP_HISTOGRAM) && (o.fused || o.field_max_iterations > 0)) return ADEPT_EINVAL;
   if (o.delta_chord_mm < 0.0 || o.delta_intersection_mm < 0.0) return ADEPT_EINVAL;
   if (o.delta_chord_mm == 0.0) o.delta_chord_mm = 0.25;
   if (o.delta_intersection_mm == 0.0) o.delta_intersection_mm = 0.001;

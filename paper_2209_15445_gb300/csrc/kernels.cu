@@ -166,6 +166,7 @@ static const void* transport_fn(int species, int minb) {
 
 // the kernel of species `species` for this variant: photons have no optional parts
 static const void* pick_transport(int precision, int species, int minb, int variant) {
+  if (variant & 4) return hist_transport_fn(precision, species, minb, variant);
   if (variant && species != 0) return variant_transport_fn(precision, species, minb, variant);
   return precision ? transport_fn<float>(species, minb) : transport_fn<double>(species, minb);
 }

@@ -198,12 +198,18 @@ cudaError_t launch_probe_distance(const Params& P, int prec, const double* pos, 
                                   int* next, cudaStream_t st);
 cudaError_t launch_probe_sample(const Params& P, int which, int m, int prec, double E, uint32_t event,
                                 int n, double* out, cudaStream_t st);
-// variant: bit 0 chord propagation, bit 1 multiple scattering / loss fluctuations
+// variant: bit 0 chord propagation, bit 1 multiple scattering / loss fluctuations, bit 2 the
+// step-length histogram
 int transport_max_blocks_per_sm(int precision, int species, int minb, int block, int variant);
 // a variant (1..3) of the e- (species 1) or e+ (2) kernel, 2 or 3 blocks/SM
 const void* variant_transport_fn(int precision, int species, int minb, int variant);
+// a kernel with the step-length histogram (variant 4, or 6 with the optional physics for e-
+// and e+), any species, 2 or 3 blocks/SM; chords and the histogram are not combined
+const void* hist_transport_fn(int precision, int species, int minb, int variant);
 // the variant the options of P call for
-inline int transport_variant(const Params& P) { return (P.chord_iter > 0 ? 1 : 0) | (P.physics ? 2 : 0); }
+inline int transport_variant(const Params& P) {
+  return (P.chord_iter > 0 ? 1 : 0) | (P.physics ? 2 : 0) | (P.steplen ? 4 : 0);
+}
 // orthographic camera of the ray tracer: the image centre, the unit right, up and view vectors
 struct RayCam {
   double o[3], right[3], up[3], d[3];

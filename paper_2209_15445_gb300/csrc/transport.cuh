@@ -118,7 +118,8 @@ enum Outcome { kDead = 0, kAlive = 1, kInteract = 2 };
 // (process 4), recorded there with its exit state (+0.9 %). The variant V compiles
 // in the optional parts, kept out of the kernels that do not use them: bit 0 the chord
 // propagator of the field (P.chord_iter > 0), bit 1 multiple scattering and loss
-// fluctuations (P.physics).
+// fluctuations (P.physics), bit 2 the validation histogram of step lengths (P.steplen;
+// its never-taken branch cost the default kernels 1.6 %).
 template <class R, int S, int V = 0>
 __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>& sec, double& dep, int& dep_bin,
                                               uint32_t& pstep, int& proc) {
@@ -221,11 +222,13 @@ __device__ __forceinline__ int step_transport(const Params& P, Trk<R>& t, Ixn<R>
   }
   if (boundary && P.geo.kind == 0 && next >= 0) t.z = __ldg(P.geo.bnd + (t.u[2] > (R)0 ? vol + 1 : vol));
   t.step = step + 1;
-  if (P.steplen && s > (R)0 && s < M<R>::big()) {
-    // validation histogram of step lengths: bin = floor(log2 s[mm]) + 40
-    int b = ilogb(s) + 40;
-    b = b < 0 ? 0 : (b > 63 ? 63 : b);
-    atomicAdd(P.steplen + 64 * S + b, 1ull);
+  if constexpr ((V & 4) != 0) {
+    if (P.steplen && s > (R)0 && s < M<R>::big()) {
+      // validation histogram of step lengths: bin = floor(log2 s[mm]) + 40
+      int b = ilogb(s) + 40;
+      b = b < 0 ? 0 : (b > 63 ? 63 : b);
+      atomicAdd(P.steplen + 64 * S + b, 1ull);
+    }
   }
 
   // S7: continuous loss by inverting the range table; optionally a Gaussian loss about

@@ -67,7 +67,7 @@ def test_cuts(A):
     dict(msc_range_factor=-1.0), dict(field_max_iterations=-1), dict(fused=1, field_max_iterations=10),
     dict(fused=1, physics=1), dict(delta_chord_mm=-1.0), dict(block_size=48), dict(block_size=512),
     dict(block_size=16), dict(graph_generations=-2), dict(graph_generations=2000),
-    dict(max_vacuum_steps=70000),
+    dict(max_vacuum_steps=70000), dict(flags=8, fused=1), dict(flags=8, field_max_iterations=10),
 ])
 def test_options(A, opts):
     assert init(A, **opts) == A.EINVAL, opts
