@@ -458,7 +458,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     if (o.fused) {
       int mb = o.blocks_per_sm > 0 ? o.blocks_per_sm : (o.precision ? 2 : 1);
       c->fminb = std::min(4, mb);
-      const int bps = fused_max_blocks_per_sm(o.precision, c->fminb, o.block_size);
+      const int bps = fused_max_blocks_per_sm(o.precision, c->fminb, o.block_size, transport_variant(P));
       c->fgrid = sms * (bps < 1 ? 1 : bps);
     }
   }

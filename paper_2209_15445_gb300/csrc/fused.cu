@@ -21,7 +21,7 @@ __device__ __forceinline__ uint32_t next_first(uint32_t first, uint32_t len, uin
   return first + k * stride - len;
 }
 
-template <class R, int MINB>
+template <class R, int MINB, int V>
 __global__ void __launch_bounds__(256, MINB) k_fused_generation(Params P, uint32_t gk) {
   __shared__ WarpRing<R> rings[8];
   __shared__ unsigned long long s_cnt[6];
@@ -42,11 +42,11 @@ __global__ void __launch_bounds__(256, MINB) k_fused_generation(Params P, uint32
   const uint32_t T0 = (n0 + 31) >> 5, T1 = (n1 + 31) >> 5, T2 = (n2 + 31) >> 5;
   uint32_t nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};  // per warp, this generation
   uint32_t first = blockIdx.x * wpb + (threadIdx.x >> 5);
-  run_tiles<R, 0>(P, p, cw, first, T0, nwarps, n0, ring, nsteps, ncreated);
+  run_tiles<R, 0, V>(P, p, cw, first, T0, nwarps, n0, ring, nsteps, ncreated);
   first = next_first(first, T0, nwarps);
-  run_tiles<R, 1>(P, p, cw, first, T1, nwarps, n1, ring, nsteps, ncreated);
+  run_tiles<R, 1, V>(P, p, cw, first, T1, nwarps, n1, ring, nsteps, ncreated);
   first = next_first(first, T1, nwarps);
-  run_tiles<R, 2>(P, p, cw, first, T2, nwarps, n2, ring, nsteps, ncreated);
+  run_tiles<R, 2, V>(P, p, cw, first, T2, nwarps, n2, ring, nsteps, ncreated);
   if ((threadIdx.x & 31) == 0)
     for (int k = 0; k < 3; ++k) {
       if (nsteps[k]) atomicAdd(&s_cnt[k], (unsigned long long)nsteps[k]);
@@ -60,15 +60,23 @@ __global__ void __launch_bounds__(256, MINB) k_fused_generation(Params P, uint32
   }
 }
 
-// Variants: FP32 physics for 2 or 3 resident 256-thread blocks per SM, FP64 for 1 or 2.
-static const void* fused_fn(int precision, int minb) {
-  if (precision) return minb >= 3 ? (const void*)k_fused_generation<float, 3> : (const void*)k_fused_generation<float, 2>;
-  return minb >= 2 ? (const void*)k_fused_generation<double, 2> : (const void*)k_fused_generation<double, 1>;
+// Variants: FP32 physics for 2 or 3 resident 256-thread blocks per SM, FP64 for 1 or 2;
+// each without (V = 0) and with (V = 8) the helix in a field. The fused kernel has no other
+// optional part (adept_init refuses chords, the optional physics and the histogram with it).
+template <int V>
+static const void* fused_by(int precision, int minb) {
+  if (precision)
+    return minb >= 3 ? (const void*)k_fused_generation<float, 3, V> : (const void*)k_fused_generation<float, 2, V>;
+  return minb >= 2 ? (const void*)k_fused_generation<double, 2, V> : (const void*)k_fused_generation<double, 1, V>;
+}
+static const void* fused_fn(int precision, int minb, int variant) {
+  return (variant & 8) ? fused_by<8>(precision, minb) : fused_by<0>(precision, minb);
 }
 
-int fused_max_blocks_per_sm(int precision, int minb, int block) {
+int fused_max_blocks_per_sm(int precision, int minb, int block, int variant) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_fn(precision, minb), block, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_fn(precision, minb, variant), block, 0) != cudaSuccess)
+    return 0;
   return n;
 }
 
@@ -84,7 +92,7 @@ cudaError_t launch_fused_generation(const Params& P, uint32_t gk, int precision,
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelExC(&cfg, fused_fn(precision, minb), args);
+  return cudaLaunchKernelExC(&cfg, fused_fn(precision, minb, transport_variant(P)), args);
 }
 
 }  // namespace adept

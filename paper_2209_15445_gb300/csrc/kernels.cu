@@ -164,10 +164,12 @@ static const void* transport_fn(int species, int minb) {
   return species == 0 ? transport_fn<R, 0>(minb) : (species == 1 ? transport_fn<R, 1>(minb) : transport_fn<R, 2>(minb));
 }
 
-// the kernel of species `species` for this variant: photons have no optional parts
+// the kernel of species `species` for this variant: photons have no optional parts and
+// move straight in any field
 static const void* pick_transport(int precision, int species, int minb, int variant) {
   if (variant & 4) return hist_transport_fn(precision, species, minb, variant);
-  if (variant && species != 0) return variant_transport_fn(precision, species, minb, variant);
+  if (species != 0 && (variant & 3)) return variant_transport_fn(precision, species, minb, variant);
+  if (species != 0 && (variant & 8)) return field_transport_fn(precision, species, minb);
   return precision ? transport_fn<float>(species, minb) : transport_fn<double>(species, minb);
 }
 

@@ -199,16 +199,22 @@ cudaError_t launch_probe_distance(const Params& P, int prec, const double* pos, 
 cudaError_t launch_probe_sample(const Params& P, int which, int m, int prec, double E, uint32_t event,
                                 int n, double* out, cudaStream_t st);
 // variant: bit 0 chord propagation, bit 1 multiple scattering / loss fluctuations, bit 2 the
-// step-length histogram
+// step-length histogram, bit 3 the helix in the field
 int transport_max_blocks_per_sm(int precision, int species, int minb, int block, int variant);
-// a variant (1..3) of the e- (species 1) or e+ (2) kernel, 2 or 3 blocks/SM
+// a variant (1..3, or 10: the optional physics in the field) of the e- (species 1) or e+ (2)
+// kernel, 2 or 3 blocks/SM
 const void* variant_transport_fn(int precision, int species, int minb, int variant);
+// the default e- or e+ kernel with the helix (variant 8), 1..4 blocks/SM
+const void* field_transport_fn(int precision, int species, int minb);
 // a kernel with the step-length histogram (variant 4, or 6 with the optional physics for e-
-// and e+), any species, 2 or 3 blocks/SM; chords and the histogram are not combined
+// and e+, each + 8 in the field), any species, 2 or 3 blocks/SM; chords and the histogram
+// are not combined
 const void* hist_transport_fn(int precision, int species, int minb, int variant);
 // the variant the options of P call for
 inline int transport_variant(const Params& P) {
-  return (P.chord_iter > 0 ? 1 : 0) | (P.physics ? 2 : 0) | (P.steplen ? 4 : 0);
+  // chords carry their own helix (chord_step)
+  return (P.chord_iter > 0 ? 1 : 0) | (P.physics ? 2 : 0) | (P.steplen ? 4 : 0) |
+         (P.field_T != 0.0 && P.chord_iter <= 0 ? 8 : 0);
 }
 // orthographic camera of the ray tracer: the image centre, the unit right, up and view vectors
 struct RayCam {
@@ -225,6 +231,6 @@ cudaError_t launch_probe_continuous(const Params& P, int which, int species, int
 // generation gen + gk of all species in one kernel
 cudaError_t launch_fused_generation(const Params& P, uint32_t gk, int precision, int minb, int grid, int block,
                                     bool pdl, cudaStream_t st);
-int fused_max_blocks_per_sm(int precision, int minb, int block);
+int fused_max_blocks_per_sm(int precision, int minb, int block, int variant);
 
 }  // namespace adept

@@ -1,6 +1,7 @@
 // The e- and e+ generation kernels with optional parts compiled in, chosen by the options:
 // V = 1 the chord propagator of the field (paper Sec. 2.3; field_max_iterations > 0),
-// V = 2 multiple scattering and loss fluctuations (physics != 0), V = 3 both. A translation
+// V = 2 multiple scattering and loss fluctuations (physics != 0), V = 3 both, V = 10 the
+// optional physics with the analytic helix in a field. A translation
 // unit of their own, so that they build in parallel with the default kernels, which carry
 // none of this code.
 #include <cuda_runtime.h>
@@ -17,9 +18,8 @@ static const void* by_minb(int minb) {
 
 template <class R, int S>
 static const void* by_variant(int minb, int variant) {
-  if (variant == 1) return by_minb<R, S, 1>(minb);
-  if (variant == 2) return by_minb<R, S, 2>(minb);
-  return by_minb<R, S, 3>(minb);
+  if (variant & 1) return (variant & 2) ? by_minb<R, S, 3>(minb) : by_minb<R, S, 1>(minb);
+  return (variant & 8) ? by_minb<R, S, 10>(minb) : by_minb<R, S, 2>(minb);
 }
 
 const void* variant_transport_fn(int precision, int species, int minb, int variant) {
