@@ -131,7 +131,8 @@ typedef struct {
   int32_t graph_generations;  /* generations per captured CUDA graph [32]; -1 = no graphs:
                                  launch each generation and read the queue sizes after it */
   uint32_t seed;              /* Philox key word 0 [1] */
-  uint32_t process_mask;      /* ADEPT_P_* bits, 0 = all [0] */
+  uint32_t process_mask;      /* ADEPT_P_* bits, 0 = all [0]; a process switched off has zero
+                                 cross-section tables in the context (adept_get_table) */
   uint32_t max_steps;         /* per-track step cap; the rest of the energy is "killed" [100000] */
   uint32_t max_vacuum_steps;  /* consecutive vacuum-step cap [1000] */
   uint32_t max_events;        /* event slots (events in flight) [65536] */

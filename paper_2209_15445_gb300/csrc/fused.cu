@@ -40,13 +40,14 @@ __global__ void __launch_bounds__(256, MINB) k_fused_generation(Params P, uint32
   const uint32_t n1 = min(__ldcg(&P.ctrl->count[cr][1].n), P.cap);
   const uint32_t n2 = min(__ldcg(&P.ctrl->count[cr][2].n), P.cap);
   const uint32_t T0 = (n0 + 31) >> 5, T1 = (n1 + 31) >> 5, T2 = (n2 + 31) >> 5;
-  uint32_t nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};  // per warp, this generation
+  uint32_t nsteps[3] = {0, 0, 0}, ncreated[3] = {0, 0, 0};  // this generation: steps per lane, secondaries per warp
   uint32_t first = blockIdx.x * wpb + (threadIdx.x >> 5);
   run_tiles<R, 0, V>(P, p, cw, first, T0, nwarps, n0, ring, nsteps, ncreated);
   first = next_first(first, T0, nwarps);
   run_tiles<R, 1, V>(P, p, cw, first, T1, nwarps, n1, ring, nsteps, ncreated);
   first = next_first(first, T1, nwarps);
   run_tiles<R, 2, V>(P, p, cw, first, T2, nwarps, n2, ring, nsteps, ncreated);
+  for (int k = 0; k < 3; ++k) nsteps[k] = __reduce_add_sync(0xFFFFFFFFu, nsteps[k]);
   if ((threadIdx.x & 31) == 0)
     for (int k = 0; k < 3; ++k) {
       if (nsteps[k]) atomicAdd(&s_cnt[k], (unsigned long long)nsteps[k]);

@@ -104,7 +104,10 @@ __device__ inline void put(double2* d64, float2* d32, size_t at, const double* r
   d32[at] = make_float2((float)a, (float)(b - a));
 }
 
-__global__ void k_pack(const MatDev* mats, int n_mat, BuildScratch s, PackOut o) {
+// Packs the raw rows into (value, slope) records. A process switched off by the process mask
+// (tests of one process at a time) gets a zero cross-section table, so that the step needs
+// no test of the mask: its lookup gives exactly 0, as a skipped one did.
+__global__ void k_pack(const MatDev* mats, int n_mat, BuildScratch s, PackOut o, uint32_t mask) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n_mat * kNNode) return;
   const int m = idx / kNNode, i = idx % kNNode;
@@ -124,6 +127,17 @@ __global__ void k_pack(const MatDev* mats, int n_mat, BuildScratch s, PackOut o)
   for (int t = 0; t < kNTabG; ++t) put(o.g64, o.g32, r * kNTabG + t, v + grow[t] * kNNode, i);
   for (int t = 0; t < kNTabE; ++t) put(o.e64, o.e32, r * kNTabE + t, v + erow[t] * kNNode, i);
   for (int t = 0; t < kNTabP; ++t) put(o.p64, o.p32, r * kNTabP + t, v + prow[t] * kNNode, i);
+  if (mask) {
+    // process bits: gamma Compton, pair, photo (tables 0-2); e- ionisation, brems (tables
+    // 2-3); e+ ionisation, brems, annihilation (tables 2-4)
+    auto off = [&](double2* d64, float2* d32, size_t at) { d64[at] = make_double2(0, 0); d32[at] = make_float2(0, 0); };
+    for (int t = 0; t < 3; ++t)
+      if (!(mask & (1u << t))) off(o.g64, o.g32, r * kNTabG + t);
+    for (int t = 2; t < 4; ++t)
+      if (!(mask & (1u << (t + 1)))) off(o.e64, o.e32, r * kNTabE + t);
+    for (int t = 2; t < 5; ++t)
+      if (!(mask & (1u << (t + 3)))) off(o.p64, o.p32, r * kNTabP + t);
+  }
   o.re64[r] = v[V_RE * kNNode + i];
   o.rp64[r] = v[V_RP * kNNode + i];
   o.re32[r] = (float)v[V_RE * kNNode + i];
@@ -134,7 +148,6 @@ cudaError_t launch_build_tables(const Params& P, const double* mat_in, int n_mat
                                 BuildScratch s, double2* g64, double2* e64, double2* p64, float2* g32,
                                 float2* e32, float2* p32, double* re64, double* rp64, float* re32, float* rp32,
                                 double* Tc, double* kc, cudaStream_t st) {
-  (void)P;
   const int nn = n_mat * kNNode;
   const int B = 128;
   k_materials<<<1, 32, 0, st>>>(mat_in, n_mat, mat);
@@ -143,7 +156,7 @@ cudaError_t launch_build_tables(const Params& P, const double* mat_in, int n_mat
   k_charged<<<(nn + B - 1) / B, B, 0, st>>>(mat, n_mat, s, Tc, kc);
   k_ranges<<<1, 32, 0, st>>>(mat, n_mat, s);
   PackOut o{g64, e64, p64, g32, e32, p32, re64, rp64, re32, rp32};
-  k_pack<<<(nn + B - 1) / B, B, 0, st>>>(mat, n_mat, s, o);
+  k_pack<<<(nn + B - 1) / B, B, 0, st>>>(mat, n_mat, s, o, P.process_mask);
   return cudaGetLastError();
 }
 
