@@ -684,9 +684,10 @@ static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b, bool captu
     // fork e- (main stream), e+ and gamma (side streams), join
     for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->side[j], c->fork, 0);
     cudaStream_t st[3] = {c->side[1], c->stream, c->side[0]};  // gamma, e-, e+
-    // launch order e-, e+, gamma: measured 2 % faster than gamma first on the 10 GeV showers
-    // (the gamma kernel, the largest, then fills the SMs as the charged kernels drain)
-    for (int sp : {1, 2, 0}) {
+    // launch order gamma, e+, e-: on the 10 GeV showers 2.4 % faster than e-, e+, gamma with
+    // the current kernels (e+ at 3 blocks per SM); the order mattered the other way round when
+    // the e+ kernel ran at 2
+    for (int sp : {0, 2, 1}) {
       if (e == cudaSuccess)
         e = launch_transport(c->P, (uint32_t)k, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, k > 0,
                              st[sp]);
@@ -753,7 +754,7 @@ static int capture_tail_graph(adept_ctx* c, int b) {
       e = cudaEventRecord(c->fork, s0);
       for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(c->side[j], c->fork, 0);
       cudaStream_t st[3] = {c->side[1], s0, c->side[0]};  // gamma, e-, e+
-      for (int sp : {1, 2, 0})
+      for (int sp : {0, 2, 1})
         if (e == cudaSuccess) e = launch_transport(c->P, kGkDevice, c->opt.precision, sp, c->minb[sp], c->grid[sp], c->block, false, st[sp]);
       for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventRecord(c->join[j], c->side[j]);
       for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(s0, c->join[j], 0);

@@ -462,7 +462,6 @@ __device__ __forceinline__ void run_tiles(const Params& P, int p, int cw, uint32
     }
     // S10: score the step's deposit in (event, layer, material)
     score(P, t.ev, bin, dep);
-    __syncwarp();
     emit<R, S>(P, p, cw, t, outcome == kAlive, sec, pstep, ncreated);
     if (phase_a) {
       const uint32_t need = __ballot_sync(0xFFFFFFFFu, outcome == kInteract);
@@ -526,7 +525,7 @@ __global__ void __launch_bounds__(256, MINB) k_transport(Params P, uint32_t gk) 
   const uint32_t gen = __ldcg(&P.ctrl->gen) + gk;
   const int p = gen & 1;
   if (threadIdx.x == 0) { s_steps = 0; s_created[0] = s_created[1] = s_created[2] = 0; }
-  // the e- kernel is launched first of the three
+  // one block of the e- kernel does the bookkeeping (any of the three could)
   if (S == 1 && blockIdx.x == 0 && threadIdx.x == 0) open_generation(P, gen, gk);
   __syncthreads();
   // injection may have counted past the capacity (those tracks were dropped)
