@@ -71,6 +71,8 @@ def args_parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 form on the same workload")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--fp64-warmup", type=int, default=1)
+    ap.add_argument("--one-events", type=int, default=20,
+                    help="events of the FP64 one-event-per-launch sample in fp64_form")
     ap.add_argument("--arena-gb", type=float, default=10.0)
     ap.add_argument("--bps", type=int, default=0, help="transport-kernel blocks/SM variant (0 = library default)")
     ap.add_argument("--bps-species", type=str, default="", help="per-species variants gamma,e-,e+")
@@ -386,6 +388,25 @@ def run_ours(a):
                 "split_over_fp64": value / (st64 / (ms64 / 1e3))}
         t64.close()
         del dev64
+        # the plain FP64 form one event per transport, one generation per launch with the
+        # queue sizes read back after each (no graphs), on a sample of the same events
+        t1 = A.Transport(geom, precision=0, arena_bytes=1 << 30, graph_generations=-1, max_events=1024)
+        one = [A.tracks_array(prim.take([i])) for i in range(a.one_events + 1)]
+        rid = t1.submit(one[-1]); t1.transport(); t1.result(rid, 1)  # warm-up
+        g0 = t1.stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(a.one_events):
+            rid = t1.submit(one[k]); t1.transport(); t1.result(rid, 1)
+        torch.cuda.synchronize()
+        dt1 = time.perf_counter() - t0
+        g1 = t1.stats()
+        t1.close()
+        st1 = sum(g1.steps) - sum(g0.steps)
+        fp64["one_event_per_launch"] = {"value": st1 / dt1, "unit": UNIT, "showers_per_s": a.one_events / dt1,
+                                        "events": a.one_events, "ms_per_event": 1e3 * dt1 / a.one_events,
+                                        "gpu_launches_per_event": (g1.launches - g0.launches) / a.one_events,
+                                        "split_over_this": value / (st1 / dt1)}
 
     base = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
