@@ -708,8 +708,9 @@ static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b, bool captu
 
 // Below adept_options.tail_tracks live tracks a generation is dominated by its launch, and
 // a tail chunk trades the programmatic launch between generations (about 5 us a generation
-// on GB300) for stopping exactly when the last track dies (a fixed chunk runs to its end and
-// one more is queued behind it, both empty at the end of a transport). So tail chunks are
+// on GB300) for stopping exactly when the last track dies (a fixed chunk runs to its end, and
+// one more is queued behind it: at the end of a transport the rest of the one and all of the
+// other run on empty queues). So tail chunks are
 // kept for the decay at the end: fewer live tracks than tail_tracks and than a kTailDecay-th
 // of the peak since the queues were last empty. A tail chunk runs at most
 // graph_generations generations, like a fixed one, so the status is read as often.
