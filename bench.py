@@ -45,7 +45,7 @@ TRACK_BYTES_SPLIT = 64  # x,y,z f64 + direction 3 f32 + E f64 + id u64 + event, 
 # for the split form, profiles/transport_kernels_10gev_e_showers_fp64_gen60_full.md for the
 # plain FP64 form); valid while the kernel sources hash to NCU_SRC_HASH, null otherwise
 NCU_BYTES_PER_STEP = {1: 107.9, 0: 132.0}
-NCU_SRC_HASH = "1194fd521cae92bb"
+NCU_SRC_HASH = "8b75337b026b226d"
 
 
 def kernel_src_hash() -> str:
@@ -312,7 +312,7 @@ def run_ours(a):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "kernel": ("k_fused_generation<%s> (one launch = one generation, all species)" if tr.options.fused else
-                       "k_transport<%s, species> x3, concurrent (one launch = one generation: e-, e+, gamma)")
+                       "k_transport<%s, species> x3, concurrent (one launch = one generation: gamma, e+, e-)")
                       % ("float" if a.precision else "double"),
             "alg_bytes_per_launch": alg_bytes / kern_n if kern_n else None,
             "mean_launch_us": 1e3 * kern_ms / kern_n if kern_n else None,

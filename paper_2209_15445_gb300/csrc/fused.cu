@@ -75,10 +75,7 @@ static const void* fused_fn(int precision, int minb, int variant) {
 }
 
 int fused_max_blocks_per_sm(int precision, int minb, int block, int variant) {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_fn(precision, minb, variant), block, 0) != cudaSuccess)
-    return 0;
-  return n;
+  return max_blocks_small_carveout(fused_fn(precision, minb, variant), block);
 }
 
 cudaError_t launch_fused_generation(const Params& P, uint32_t gk, int precision, int minb, int grid, int block,

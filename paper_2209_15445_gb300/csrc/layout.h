@@ -201,6 +201,9 @@ cudaError_t launch_probe_sample(const Params& P, int which, int m, int prec, dou
 // variant: bit 0 chord propagation, bit 1 multiple scattering / loss fluctuations, bit 2 the
 // step-length histogram, bit 3 the helix in the field
 int transport_max_blocks_per_sm(int precision, int species, int minb, int block, int variant);
+// resident blocks of `block` threads per SM for kernel fn, after asking for the smallest
+// shared-memory carveout that still holds them (the rest of the SM's memory stays L1)
+int max_blocks_small_carveout(const void* fn, int block);
 // a variant (1..3, or 10: the optional physics in the field) of the e- (species 1) or e+ (2)
 // kernel, 2 or 3 blocks/SM
 const void* variant_transport_fn(int precision, int species, int minb, int variant);
