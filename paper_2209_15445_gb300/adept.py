@@ -421,10 +421,17 @@ class Transport:
         self.check(rc)
         return arr
 
-    def result(self, rid, n_events):
-        out = np.zeros((n_events, self.n_bins))
+    def result(self, rid, n_events, out=None):
+        """(edep[n_events, n_bins], meta) of a finished request; `out`, if given, is a float64
+        array of that shape to fill (reused across requests, it saves the pages of a new one)"""
+        if out is None:
+            out = np.empty((n_events, self.n_bins))
+        elif out.shape != (n_events, self.n_bins) or out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError(f"out must be a C-contiguous float64 array of shape {(n_events, self.n_bins)}")
+        # the library writes the request's rows; only rows past them need zeros
         rc, meta = adept_get_scoring(self.h, rid, out)
         self.check(rc)
+        out[meta.n_events:] = 0.0
         return out, meta
 
     def run(self, prim, timeout_us=0):

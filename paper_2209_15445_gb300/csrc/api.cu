@@ -32,7 +32,16 @@ static_assert(offsetof(adept_track, event) == offsetof(TrackIn, event), "adept_t
 namespace {
 
 using Clock = std::chrono::steady_clock;
-constexpr uint32_t kDoneChunk = 4096;  // done-list entries copied back with each status read
+
+// Host copy of a finished request's rows (deposits [event][bin], then leaked and killed per
+// event): a pinned block from the context's pool, so that the copy out of device memory runs
+// at the link's rate and reuses pages already mapped, or pageable memory if pinning fails.
+struct ResultBuf {
+  double* p = nullptr;
+  size_t cap = 0;  // doubles
+  bool pinned = false;
+  std::vector<double> pageable;
+};
 
 struct Request {
   uint32_t id = 0;
@@ -46,7 +55,7 @@ struct Request {
   uint32_t remaining = 0;              // events not finished
   int state = 0;                       // 0 pending, 1 in flight, 2 done
   Clock::time_point t_submit, t_done;
-  std::vector<double> edep, leaked, killed;
+  ResultBuf res;                       // rows copied back at completion
   std::vector<adept_track> outgoing;   // particles that left the calorimeter
 };
 
@@ -124,6 +133,12 @@ struct adept_ctx {
   cudaStream_t submit_stream = nullptr;      // device submissions' field reads (producer threads)
   char* h_stage = nullptr;
   size_t h_stage_bytes = 0;
+  char* h_sub = nullptr;                     // device submissions' tracks read back (under submit_mu)
+  size_t h_sub_bytes = 0;
+  // pinned blocks for finished requests' rows: free ones, and all (freed at destroy)
+  std::mutex pool_mu;
+  std::vector<std::pair<double*, size_t>> pool_free;
+  std::vector<double*> pool_all;
   // launch shape
   int grid[3] = {0, 0, 0}, block = 256, minb[3] = {1, 1, 1};  // per species
   int fgrid = 0, fminb = 0;  // fused generation kernel
@@ -424,10 +439,21 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     CK(cudaMemcpyAsync(qdesc, &P.q[0][0], sizeof(TrackSoA) * 6, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(steplen, 0, sizeof(unsigned long long) * 3 * 64, c->stream));
     CK(cudaMemsetAsync(E.state, 0, sizeof(uint32_t) * ms, c->stream));
+    // the chunk status buffers are mapped: the finish pass writes them and the chunk's first
+    // kernel reads the floor, with no copy in the stream between two chunks
     for (int b = 0; b < 2; ++b) {
-      CK(cudaHostAlloc(&c->h_ctrl[b], sizeof(Ctrl), cudaHostAllocDefault));
-      CK(cudaHostAlloc(&c->h_floor[b], sizeof(unsigned long long), cudaHostAllocDefault));
-      CK(cudaHostAlloc(&c->h_done[b], sizeof(uint32_t) * kDoneChunk, cudaHostAllocDefault));
+      CK(cudaHostAlloc(&c->h_ctrl[b], sizeof(Ctrl), cudaHostAllocMapped));
+      CK(cudaHostAlloc(&c->h_floor[b], sizeof(unsigned long long), cudaHostAllocMapped));
+      CK(cudaHostAlloc(&c->h_done[b], sizeof(uint32_t) * kDoneChunk, cudaHostAllocMapped));
+      memset(c->h_ctrl[b], 0, sizeof(Ctrl));
+      *c->h_floor[b] = 0;
+      void* d = nullptr;
+      CK(cudaHostGetDevicePointer(&d, c->h_ctrl[b], 0));
+      P.h_ctrl[b] = static_cast<Ctrl*>(d);
+      CK(cudaHostGetDevicePointer(&d, c->h_done[b], 0));
+      P.h_done[b] = static_cast<uint32_t*>(d);
+      CK(cudaHostGetDevicePointer(&d, c->h_floor[b], 0));
+      P.h_floor[b] = static_cast<const unsigned long long*>(d);
       CK(cudaEventCreateWithFlags(&c->status_ev[b], cudaEventDisableTiming));
     }
     CK(cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
@@ -484,21 +510,35 @@ extern "C" int adept_build_tables(adept_ctx* c) {
 // within their event
 template <class FE, class FP, class FX>
 static int prepare_request(adept_ctx* c, Request& r, FE ev_at, FP pdg_at, FX e_at) {
-  std::unordered_map<uint32_t, uint32_t> idx;
+  // event number -> index into r.keys: open addressing in a power-of-two table of at least 2n
+  // slots (tv holds index + 1, 0 = empty); consecutive tracks of one event skip the lookup
+  int bits = 4;
+  while (((size_t)1 << bits) < 2 * r.n && bits < 31) ++bits;
+  const uint32_t tmask = (1u << bits) - 1u;
+  std::vector<uint32_t> tk((size_t)1 << bits), tv((size_t)1 << bits, 0u);
   std::vector<uint32_t> count;
   r.meta.resize(2 * r.n);
   r.energy = 0.0;
+  uint32_t last_ev = 0, last_k = 0xFFFFFFFFu;
   for (size_t i = 0; i < r.n; ++i) {
     const uint32_t ev = ev_at(i);
-    auto it = idx.find(ev);
     uint32_t k;
-    if (it == idx.end()) {
-      k = (uint32_t)r.keys.size();
-      idx.emplace(ev, k);
-      r.keys.push_back(ev);
-      count.push_back(0);
+    if (ev == last_ev && last_k != 0xFFFFFFFFu) {
+      k = last_k;
     } else {
-      k = it->second;
+      uint32_t h = (ev * 2654435761u) >> (32 - bits);
+      while (tv[h] != 0u && tk[h] != ev) h = (h + 1u) & tmask;
+      if (tv[h] == 0u) {
+        k = (uint32_t)r.keys.size();
+        tk[h] = ev;
+        tv[h] = k + 1u;
+        r.keys.push_back(ev);
+        count.push_back(0);
+      } else {
+        k = tv[h] - 1u;
+      }
+      last_ev = ev;
+      last_k = k;
     }
     r.meta[2 * i] = k;
     r.meta[2 * i + 1] = ++count[k];
@@ -559,18 +599,25 @@ extern "C" int adept_submit_device(adept_ctx* c, const void* dev_tracks, size_t 
   std::vector<int32_t> pdg(n);
   std::vector<double> E(n);
   if (n) {
-    // read back the three fields the host needs for numbering and admission
-    const char* base = static_cast<const char*>(dev_tracks);
-    // (on a stream of its own: a producer must not wait for the transport's queued work)
+    // read back the tracks in one contiguous copy into pinned memory and keep the three fields
+    // the host needs for numbering and admission (three strided copies of 4- and 8-byte rows
+    // took 0.5 ms for 10^4 tracks); on a stream of its own: a producer must not wait for the
+    // transport's queued work
     cudaStream_t ss = c->submit_stream;
     std::lock_guard<std::mutex> lk(c->submit_mu);
-    CK(cudaMemcpy2DAsync(ev.data(), 4, base + offsetof(adept_track, event), sizeof(adept_track), 4, n,
-                         cudaMemcpyDeviceToHost, ss));
-    CK(cudaMemcpy2DAsync(pdg.data(), 4, base + offsetof(adept_track, pdg), sizeof(adept_track), 4, n,
-                         cudaMemcpyDeviceToHost, ss));
-    CK(cudaMemcpy2DAsync(E.data(), 8, base + offsetof(adept_track, E_kin_MeV), sizeof(adept_track), 8, n,
-                         cudaMemcpyDeviceToHost, ss));
+    const size_t bytes = sizeof(adept_track) * n;
+    if (c->h_sub_bytes < bytes) {
+      if (c->h_sub) CK(cudaFreeHost(c->h_sub));
+      c->h_sub = nullptr;
+      c->h_sub_bytes = 0;
+      const size_t want = std::max(bytes, (size_t)1 << 20);
+      CK(cudaHostAlloc(&c->h_sub, want, cudaHostAllocDefault));
+      c->h_sub_bytes = want;
+    }
+    CK(cudaMemcpyAsync(c->h_sub, dev_tracks, bytes, cudaMemcpyDeviceToHost, ss));
     CK(cudaStreamSynchronize(ss));
+    const adept_track* h = reinterpret_cast<const adept_track*>(c->h_sub);
+    for (size_t i = 0; i < n; ++i) { ev[i] = h[i].event; pdg[i] = h[i].pdg; E[i] = h[i].E_kin_MeV; }
   }
   int rc = prepare_request(
       c, *r, [&](size_t i) { return ev[i]; }, [&](size_t i) { return pdg[i]; }, [&](size_t i) { return E[i]; });
@@ -656,7 +703,7 @@ static bool timing_species(const adept_ctx* c) { return (c->opt.flags & ADEPT_FL
 // one after each kernel it times. tstream joins the chain only at the end of the chunk, so
 // the records never delay the next generation.
 static cudaError_t enqueue_generations(adept_ctx* c, int gens, int b, bool captured) {
-  cudaError_t e = cudaMemsetAsync(&c->P.ctrl->done_count[b], 0, sizeof(uint32_t), c->stream);
+  cudaError_t e = launch_open_chunk(c->P, b, c->stream);
   // inside a capture a timing record must be an external event node; outside, a plain record
   const unsigned rf = captured ? cudaEventRecordExternal : cudaEventRecordDefault;
   const bool T = timing(c), TS = timing_species(c);
@@ -728,7 +775,7 @@ static int capture_tail_graph(adept_ctx* c, int b) {
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  e = cudaMemsetAsync(&c->P.ctrl->done_count[b], 0, sizeof(uint32_t), c->stream);
+  e = launch_open_chunk(c->P, b, c->stream);
   if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, &g, nullptr, nullptr, nullptr);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
   if (e == cudaSuccess) e = launch_tail_open(c->P, h, c->stream);
@@ -797,10 +844,9 @@ static int capture_graph(adept_ctx* c, int gens, int b) {
 static int launch_chunk(adept_ctx* c, int b) {
   const int G = c->opt.graph_generations;
   const int gens = G > 0 ? G : 1;
-  // the outgoing ring may be written up to the host's read position plus its capacity
+  // the outgoing ring may be written up to the host's read position plus its capacity (read
+  // by the chunk's first kernel from this pinned word)
   *c->h_floor[b] = c->leak_read;
-  CK(cudaMemcpyAsync(&c->P.ctrl->leak_floor, c->h_floor[b], sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                     c->stream));
   if (timing(c)) {
     int rc = ensure_events(c, 8 * gens);
     if (rc) return rc;
@@ -815,21 +861,19 @@ static int launch_chunk(adept_ctx* c, int b) {
       if (rc) return rc;
     }
     CK(cudaGraphLaunch(c->tgraph[b], c->stream));
-    c->stats.launches += 4;  // open, end of chunk, mark, finish; the loop's kernels once read back
+    c->stats.launches += 5;  // chunk open, loop open, end of chunk, mark, finish; the loop's kernels once read back
   } else if (G > 0) {
     if (!c->graph[b]) {
       int rc = capture_graph(c, G, b);
       if (rc) return rc;
     }
     CK(cudaGraphLaunch(c->graph[b], c->stream));
-    c->stats.launches += (c->opt.fused ? 1 : 3) * gens + 3;
+    c->stats.launches += (c->opt.fused ? 1 : 3) * gens + 4;  // and chunk open, end, mark, finish
   } else {
     CK(enqueue_generations(c, 1, b, false));
-    c->stats.launches += (c->opt.fused ? 1 : 3) * gens + 3;
+    c->stats.launches += (c->opt.fused ? 1 : 3) * gens + 4;  // and chunk open, end, mark, finish
   }
-  CK(cudaMemcpyAsync(c->h_ctrl[b], c->P.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(c->h_done[b], c->P.evt.done_list[b], sizeof(uint32_t) * kDoneChunk, cudaMemcpyDeviceToHost,
-                     c->stream));
+  // the chunk's finish pass has written its status and done list to h_ctrl[b] and h_done[b]
   CK(cudaEventRecord(c->status_ev[b], c->stream));
   return ADEPT_OK;
 }
@@ -906,20 +950,64 @@ static int collect_outgoing(adept_ctx* c, const Ctrl& h, int b, int* stop_rc) {
   return ADEPT_OK;
 }
 
+// a host block of at least `need` doubles for a finished request's rows: the smallest free
+// pinned block that holds them, else a new pinned one, else pageable memory
+static void acquire_result(adept_ctx* c, ResultBuf& rb, size_t need) {
+  {
+    std::lock_guard<std::mutex> lk(c->pool_mu);
+    size_t best = c->pool_free.size();
+    for (size_t i = 0; i < c->pool_free.size(); ++i)
+      if (c->pool_free[i].second >= need && (best == c->pool_free.size() || c->pool_free[i].second < c->pool_free[best].second))
+        best = i;
+    if (best < c->pool_free.size()) {
+      rb.p = c->pool_free[best].first;
+      rb.cap = c->pool_free[best].second;
+      rb.pinned = true;
+      c->pool_free.erase(c->pool_free.begin() + (std::ptrdiff_t)best);
+      return;
+    }
+  }
+  const size_t cap = std::max<size_t>(need, 8192);
+  double* p = nullptr;
+  if (cudaHostAlloc(reinterpret_cast<void**>(&p), sizeof(double) * cap, cudaHostAllocDefault) == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(c->pool_mu);
+    c->pool_all.push_back(p);
+    rb.p = p;
+    rb.cap = cap;
+    rb.pinned = true;
+    return;
+  }
+  (void)cudaGetLastError();  // a failed pinned allocation leaves no error behind
+  rb.pageable.resize(need);
+  rb.p = rb.pageable.data();
+  rb.cap = need;
+  rb.pinned = false;
+}
+
+static void release_result(adept_ctx* c, ResultBuf& rb) {
+  if (rb.pinned) {
+    std::lock_guard<std::mutex> lk(c->pool_mu);
+    c->pool_free.emplace_back(rb.p, rb.cap);
+  }
+  rb.p = nullptr;
+  rb.cap = 0;
+  rb.pinned = false;
+  std::vector<double>().swap(rb.pageable);
+}
+
 // copy a finished request's rows back and release its slots
 static int complete(adept_ctx* c, Request* r, int b) {
   const size_t nk = r->keys.size(), nb = c->n_bins;
-  r->edep.resize(nk * nb);
-  r->leaked.resize(nk);
-  r->killed.resize(nk);
   if (nk) {
+    acquire_result(c, r->res, nk * nb + 2 * nk);
+    double* h = r->res.p;
     // the rows are final once chunk b has run; copy them while the next chunk computes
     cudaStream_t cs = c->copy_stream;
     CK(cudaStreamWaitEvent(cs, c->status_ev[b], 0));
-    CK(cudaMemcpyAsync(r->edep.data(), c->P.evt.edep + (size_t)r->slot_base * nb, sizeof(double) * nk * nb,
-                       cudaMemcpyDeviceToHost, cs));
-    CK(cudaMemcpyAsync(r->leaked.data(), c->P.evt.leaked + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost, cs));
-    CK(cudaMemcpyAsync(r->killed.data(), c->P.evt.killed + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(h, c->P.evt.edep + (size_t)r->slot_base * nb, sizeof(double) * nk * nb, cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(h + nk * nb, c->P.evt.leaked + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost, cs));
+    CK(cudaMemcpyAsync(h + nk * nb + nk, c->P.evt.killed + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost,
+                       cs));
     // a finished slot is never read again by the finish pass (state 2 or 0 are both inert)
     CK(cudaMemsetAsync(c->P.evt.state + r->slot_base, 0, sizeof(uint32_t) * nk, cs));
     CK(cudaStreamSynchronize(cs));
@@ -1057,15 +1145,35 @@ extern "C" int adept_get_scoring(adept_ctx* c, uint32_t id, double* edep_out, si
     r = std::move(it->second);
     c->reqs.erase(it);
   }
-  if (!r->edep.empty()) memcpy(edep_out, r->edep.data(), sizeof(double) * r->edep.size());
+  // copy the rows out and sum them in one pass, with eight partial sums (one dependent chain
+  // of 10^6 additions took about a millisecond)
+  const size_t nk = r->keys.size(), m = nk * (size_t)c->n_bins;
+  double d = 0, l = 0, k = 0;
+  if (nk) {
+    const double* s = r->res.p;
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    size_t i = 0;
+    for (; i + 8 <= m; i += 8)
+      for (int j = 0; j < 8; ++j) {
+        const double v = s[i + j];
+        edep_out[i + j] = v;
+        a[j] += v;
+      }
+    for (; i < m; ++i) {
+      edep_out[i] = s[i];
+      a[0] += s[i];
+    }
+    d = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    for (size_t e = 0; e < nk; ++e) {
+      l += s[m + e];
+      k += s[m + nk + e];
+    }
+    release_result(c, r->res);
+  }
   if (meta) {
     meta->request = r->id;
-    meta->n_events = (uint32_t)r->keys.size();
+    meta->n_events = (uint32_t)nk;
     meta->n_bins = (uint32_t)c->n_bins;
-    double d = 0, l = 0, k = 0;
-    for (double v : r->edep) d += v;
-    for (double v : r->leaked) l += v;
-    for (double v : r->killed) k += v;
     meta->deposited_MeV = d;
     meta->leaked_MeV = l;
     meta->killed_MeV = k;
@@ -1373,5 +1481,7 @@ extern "C" void adept_destroy(adept_ctx* c) {
   if (c->stage_ev) cudaEventDestroy(c->stage_ev);
   if (c->copy_stream) { cudaStreamSynchronize(c->copy_stream); cudaStreamDestroy(c->copy_stream); }
   if (c->h_stage) cudaFreeHost(c->h_stage);
+  if (c->h_sub) cudaFreeHost(c->h_sub);
+  for (double* p : c->pool_all) cudaFreeHost(p);
   delete c;
 }

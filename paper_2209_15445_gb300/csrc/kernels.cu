@@ -319,6 +319,10 @@ __global__ void k_mark(Params P) {
   }
 }
 
+// The done list goes to device memory and, for its first kDoneChunk entries, straight to the
+// host's pinned copy of buffer b; the last block to end then writes the whole Ctrl there. The
+// host reads both once the chunk has ended, and no copy runs between two chunks (two
+// device-to-host copies and one host-to-device copy a chunk boundary before).
 __global__ void k_finish(Params P, int b) {
   const uint32_t gen = __ldcg(&P.ctrl->gen);
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < P.evt.max_slots; s += gridDim.x * blockDim.x) {
@@ -326,8 +330,34 @@ __global__ void k_finish(Params P, int b) {
       P.evt.state[s] = 2u;
       const uint32_t k = atomicAdd(&P.ctrl->done_count[b], 1u);
       P.evt.done_list[b][k] = s;
+      if (k < kDoneChunk) P.h_done[b][k] = s;
     }
   }
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&P.ctrl->finish_ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) P.ctrl->finish_ticket = 0;
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(P.ctrl);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(P.h_ctrl[b]);
+  for (uint32_t i = threadIdx.x; i < sizeof(Ctrl) / 4; i += blockDim.x) dst[i] = __ldcg(src + i);
+  __threadfence_system();
+}
+
+// Start of a chunk: the outgoing-ring read position the host left in its pinned copy of
+// buffer b, and an empty done count for the chunk's finish pass. One thread.
+__global__ void k_open_chunk(Params P, int b) {
+  if (threadIdx.x != 0) return;
+  P.ctrl->leak_floor = *reinterpret_cast<const volatile unsigned long long*>(P.h_floor[b]);
+  P.ctrl->done_count[b] = 0;
+}
+
+cudaError_t launch_open_chunk(const Params& P, int b, cudaStream_t st) {
+  k_open_chunk<<<1, 32, 0, st>>>(P, b);
+  return cudaGetLastError();
 }
 
 // Tail chunks (conditional while node): the condition that runs the next generation. Live

@@ -90,7 +90,8 @@ struct Ctrl {
   uint32_t log_n;             // rows written to the generation log
   uint32_t error;             // first device-detected error code (0 = none)
   uint32_t tail_k;            // generations a tail chunk has run so far (see kGkDevice)
-  uint32_t pad[3];
+  uint32_t finish_ticket;     // blocks of the finish pass that have ended (the last one resets it)
+  uint32_t pad[2];
   unsigned long long steps[3];
   unsigned long long created[3];
   unsigned long long overflow;
@@ -144,7 +145,14 @@ struct Params {
   double delta_chord;   // chord sagitta limit, mm
   double delta_int;     // intersection accuracy, mm
   uint32_t tail_exit;   // a tail chunk ends once this many tracks are live
+  // the host's pinned, device-mapped status of the two chunk buffers: the copy of Ctrl and the
+  // first kDoneChunk entries of the done list that a chunk's finish pass writes, and the
+  // outgoing-ring read position its first kernel reads (so no copy sits between two chunks)
+  Ctrl* h_ctrl[2];
+  uint32_t* h_done[2];
+  const unsigned long long* h_floor[2];
 };
+constexpr uint32_t kDoneChunk = 4096;  // done-list entries written to the host with each status
 
 // device view of one submitted particle; same layout as adept_track in adept.h
 struct TrackIn {
@@ -180,8 +188,11 @@ cudaError_t launch_admit(const Params& P, uint32_t slot_base, const uint32_t* ke
 // meta: per track (event index within the request, track id)
 cudaError_t launch_init_primaries(const Params& P, const TrackIn* recs, const uint32_t* meta, int n,
                                   uint32_t slot_base, int precision, cudaStream_t st);
+// start of a chunk in status buffer b: the host's outgoing-ring read position, done count 0
+cudaError_t launch_open_chunk(const Params& P, int b, cudaStream_t st);
 // end of a chunk of `gens` generations (kGkDevice: the count a tail chunk left in
-// Ctrl::tail_k): log the last one, advance gen, find finished events
+// Ctrl::tail_k): log the last one, advance gen, find finished events, and write the status
+// and the done list to the host's copy of buffer b
 cudaError_t launch_finish(const Params& P, int buffer, uint32_t gens, cudaStream_t st);
 // tail chunks: before the loop, tail_k = 0 and the condition = live tracks in the queues;
 // after each generation, ++tail_k and the condition = live tracks and tail_k < max_gens
