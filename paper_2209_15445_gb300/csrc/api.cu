@@ -125,10 +125,12 @@ struct adept_ctx {
   Ctrl* h_ctrl[2] = {nullptr, nullptr};     // status of the two chunks that may be in flight
   unsigned long long* h_floor[2] = {nullptr, nullptr};  // outgoing-ring read position at each launch
   unsigned long long leak_read = 0, leak_dropped_seen = 0;  // host read position, drops seen
-  std::vector<LeakRec> leak_tmp;
+  LeakRec* h_leak = nullptr;  // pinned staging of the outgoing records read back at a status
+  size_t h_leak_cap = 0;
   uint32_t* h_done[2] = {nullptr, nullptr};
   cudaEvent_t status_ev[2] = {nullptr, nullptr};
   cudaEvent_t stage_ev = nullptr;            // the last copy out of the pinned staging buffer
+  cudaEvent_t out_ev = nullptr;              // the last copy of outgoing records into h_leak
   cudaStream_t copy_stream = nullptr;        // result copies, overlapping the next chunk
   cudaStream_t submit_stream = nullptr;      // device submissions' field reads (producer threads)
   char* h_stage = nullptr;
@@ -168,7 +170,7 @@ struct adept_ctx {
   uint32_t next_id = 1;
   std::deque<uint32_t> pending;
   std::unordered_map<uint32_t, std::unique_ptr<Request>> reqs;
-  std::vector<uint32_t> slot_req;  // slot -> request id
+  std::vector<Request*> slot_req;  // slot -> its request while that is in flight (else null)
   SlotAlloc slots;
   double energy_in_flight = 0.0;
   size_t in_flight = 0;
@@ -372,8 +374,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
   EventView& E = P.evt;
   const uint32_t ms = o.max_events;
   ok = ok && carve_n(cp, &E.key, ms) && carve_n(cp, &E.state, ms) && carve_n(cp, &E.alive, ms) &&
-       carve_n(cp, &E.edep, (size_t)ms * c->n_bins) && carve_n(cp, &E.leaked, ms) && carve_n(cp, &E.killed, ms) &&
-       carve_n(cp, &E.done_list[0], ms) && carve_n(cp, &E.done_list[1], ms);
+       carve_n(cp, &E.edep, (size_t)ms * c->n_bins) && carve_n(cp, &E.leaked, ms) && carve_n(cp, &E.killed, ms);
   ok = ok && carve_n(cp, &P.gen_log, 3 * (size_t)o.max_generation_log);
   unsigned long long* steplen = nullptr;
   ok = ok && carve_n(cp, &steplen, 3 * 64);
@@ -444,7 +445,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     for (int b = 0; b < 2; ++b) {
       CK(cudaHostAlloc(&c->h_ctrl[b], sizeof(Ctrl), cudaHostAllocMapped));
       CK(cudaHostAlloc(&c->h_floor[b], sizeof(unsigned long long), cudaHostAllocMapped));
-      CK(cudaHostAlloc(&c->h_done[b], sizeof(uint32_t) * kDoneChunk, cudaHostAllocMapped));
+      CK(cudaHostAlloc(&c->h_done[b], sizeof(uint32_t) * ms, cudaHostAllocMapped));
       memset(c->h_ctrl[b], 0, sizeof(Ctrl));
       *c->h_floor[b] = 0;
       void* d = nullptr;
@@ -457,6 +458,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
       CK(cudaEventCreateWithFlags(&c->status_ev[b], cudaEventDisableTiming));
     }
     CK(cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->out_ev, cudaEventDisableTiming));
     CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&c->submit_stream, cudaStreamNonBlocking));
     for (int j = 0; j < 2; ++j) {
@@ -489,7 +491,7 @@ extern "C" int adept_init(adept_ctx** out, const adept_geometry* geometry, const
     }
   }
   c->slots.init(ms);
-  c->slot_req.assign(ms, 0);
+  c->slot_req.assign(ms, nullptr);
   *out = c.release();
   return ADEPT_OK;
 }
@@ -656,7 +658,7 @@ static int admit(adept_ctx* c) {
       c->pending.pop_front();
       r->state = 1;
       r->remaining = (uint32_t)r->keys.size();
-      for (uint32_t k = 0; k < r->remaining; ++k) c->slot_req[base + k] = r->id;
+      for (uint32_t k = 0; k < r->remaining; ++k) c->slot_req[base + k] = r;
       c->energy_in_flight += r->energy;
       c->in_flight++;
       c->admit_est += (uint64_t)(r->energy * c->opt.tracks_per_MeV) + r->n;
@@ -912,37 +914,68 @@ static int wait_chunk(adept_ctx* c, int b) {
   return ADEPT_OK;
 }
 
-// Outgoing particles recorded up to the end of chunk b: copy them out of the ring and give
-// each to its request. Records the device could not write (ring full) are counted; they
+// Outgoing particles recorded up to the end of chunk b, in two halves, so that the host can
+// relaunch the chunk's buffer in between: start_outgoing copies the new ring entries into
+// pinned staging on copy_stream (then out_ev) and advances the host's read position, which the
+// next launch hands the device as its floor; finish_outgoing waits for the copy and gives each
+// particle to its request. Records the device could not write (ring full) are counted; they
 // make the transport fail with ADEPT_ENOMEM like a queue overflow.
-static int collect_outgoing(adept_ctx* c, const Ctrl& h, int b, int* stop_rc) {
+static int start_outgoing(adept_ctx* c, const Ctrl& h, int b, size_t* n_out) {
+  *n_out = 0;
   const unsigned long long cap = c->P.leak_cap;
   const unsigned long long end = std::min<unsigned long long>(h.leak_count, *c->h_floor[b] + cap);
   if (end > c->leak_read) {
     const size_t n = (size_t)(end - c->leak_read);
-    c->leak_tmp.resize(n);
+    // pinned staging, grown by doubling (pageable memory would take the copy through a bounce
+    // buffer)
+    if (c->h_leak_cap < n) {
+      const size_t want = std::max<size_t>(n, std::max<size_t>(2 * c->h_leak_cap, (size_t)1 << 16));
+      if (c->h_leak) CK(cudaFreeHost(c->h_leak));
+      c->h_leak = nullptr;
+      c->h_leak_cap = 0;
+      CK(cudaHostAlloc(reinterpret_cast<void**>(&c->h_leak), sizeof(LeakRec) * want, cudaHostAllocDefault));
+      c->h_leak_cap = want;
+    }
     const size_t start = (size_t)(c->leak_read % cap);
     const size_t first = std::min<size_t>(n, (size_t)cap - start);
-    CK(cudaMemcpyAsync(c->leak_tmp.data(), c->P.leak + start, sizeof(LeakRec) * first, cudaMemcpyDeviceToHost,
-                       c->copy_stream));
+    CK(cudaMemcpyAsync(c->h_leak, c->P.leak + start, sizeof(LeakRec) * first, cudaMemcpyDeviceToHost, c->copy_stream));
     if (first < n)
-      CK(cudaMemcpyAsync(c->leak_tmp.data() + first, c->P.leak, sizeof(LeakRec) * (n - first), cudaMemcpyDeviceToHost,
+      CK(cudaMemcpyAsync(c->h_leak + first, c->P.leak, sizeof(LeakRec) * (n - first), cudaMemcpyDeviceToHost,
                          c->copy_stream));
-    CK(cudaStreamSynchronize(c->copy_stream));
-    std::lock_guard<std::mutex> lk(c->mu);
-    for (const LeakRec& x : c->leak_tmp) {
-      auto it = c->reqs.find(c->slot_req[x.slot]);
-      if (it == c->reqs.end()) continue;
-      Request* r = it->second.get();
-      adept_track t;
-      t.pdg = x.pdg;
-      t.E_kin_MeV = x.E;
-      for (int k = 0; k < 3; ++k) { t.pos_mm[k] = x.pos[k]; t.dir[k] = x.dir[k]; }
-      t.event = r->keys[x.slot - r->slot_base];
-      r->outgoing.push_back(t);
-    }
+    CK(cudaEventRecord(c->out_ev, c->copy_stream));
+    *n_out = n;
   }
   c->leak_read = std::max<unsigned long long>(c->leak_read, h.leak_count);
+  return ADEPT_OK;
+}
+
+static int finish_outgoing(adept_ctx* c, const Ctrl& h, size_t n, int* stop_rc) {
+  if (n) {
+    CK(cudaEventSynchronize(c->out_ev));
+    // runs of consecutive records of one request: one capacity check per run (about 5 ns a
+    // record: with tens of thousands a chunk, this is why it runs after the relaunch)
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (size_t i = 0; i < n;) {
+      Request* r = c->slot_req[c->h_leak[i].slot];
+      size_t j = i + 1;
+      while (j < n && c->slot_req[c->h_leak[j].slot] == r) ++j;
+      if (r) {
+        const size_t need = r->outgoing.size() + (j - i);
+        if (r->outgoing.capacity() < need) r->outgoing.reserve(std::max(2 * r->outgoing.capacity(), need));
+        for (size_t k = i; k < j; ++k) {
+          const LeakRec& x = c->h_leak[k];
+          adept_track t;
+          t.pdg = x.pdg;
+          t.E_kin_MeV = x.E;
+          t.pos_mm[0] = x.pos[0]; t.pos_mm[1] = x.pos[1]; t.pos_mm[2] = x.pos[2];
+          t.dir[0] = x.dir[0]; t.dir[1] = x.dir[1]; t.dir[2] = x.dir[2];
+          t.event = r->keys[x.slot - r->slot_base];
+          r->outgoing.push_back(t);
+        }
+      }
+      i = j;
+    }
+  }
   if (h.leak_dropped > c->leak_dropped_seen && *stop_rc == ADEPT_OK)
     *stop_rc = fail(c, ADEPT_ENOMEM, "%llu outgoing particles exceeded the ring of %u (max_outgoing); results are "
                     "incomplete", h.leak_dropped - c->leak_dropped_seen, c->P.leak_cap);
@@ -996,14 +1029,15 @@ static void release_result(adept_ctx* c, ResultBuf& rb) {
 }
 
 // copy a finished request's rows back and release its slots
-static int complete(adept_ctx* c, Request* r, int b) {
+static int complete(adept_ctx* c, Request* r) {
   const size_t nk = r->keys.size(), nb = c->n_bins;
   if (nk) {
     acquire_result(c, r->res, nk * nb + 2 * nk);
     double* h = r->res.p;
-    // the rows are final once chunk b has run; copy them while the next chunk computes
+    // the rows are final: the host has waited for the chunk that finished the request (its
+    // status event may since have been recorded again by a relaunch of the chunk's buffer);
+    // copy them while the next chunk computes
     cudaStream_t cs = c->copy_stream;
-    CK(cudaStreamWaitEvent(cs, c->status_ev[b], 0));
     CK(cudaMemcpyAsync(h, c->P.evt.edep + (size_t)r->slot_base * nb, sizeof(double) * nk * nb, cudaMemcpyDeviceToHost, cs));
     CK(cudaMemcpyAsync(h + nk * nb, c->P.evt.leaked + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost, cs));
     CK(cudaMemcpyAsync(h + nk * nb + nk, c->P.evt.killed + r->slot_base, sizeof(double) * nk, cudaMemcpyDeviceToHost,
@@ -1013,6 +1047,7 @@ static int complete(adept_ctx* c, Request* r, int b) {
     CK(cudaStreamSynchronize(cs));
   }
   std::lock_guard<std::mutex> lk(c->mu);
+  for (size_t k = 0; k < nk; ++k) c->slot_req[r->slot_base + k] = nullptr;
   c->slots.release(r->slot_base, (uint32_t)nk);
   c->energy_in_flight -= r->energy;
   if (c->energy_in_flight < 0) c->energy_in_flight = 0;
@@ -1035,6 +1070,7 @@ extern "C" int adept_transport(adept_ctx* c, uint64_t timeout_us) {
   if (!c->built) return fail(c, ADEPT_ESTATE, "adept_build_tables has not run");
   const auto t0 = Clock::now();
   std::vector<uint32_t> done;
+  std::vector<Request*> finished;
   int idle_chunks = 0;
   bool queued[2] = {false, false};
   int b = 0;
@@ -1064,36 +1100,55 @@ extern "C" int adept_transport(adept_ctx* c, uint64_t timeout_us) {
     int rc = wait_chunk(c, b);
     if (rc) return rc;
     queued[b] = false;
-    const Ctrl& h = *c->h_ctrl[b];
+    // copies of the chunk's status and done list: a relaunch of buffer b rewrites both
+    const Ctrl h = *c->h_ctrl[b];
     for (int k = 0; k < 3; ++k) { c->stats.steps[k] = h.steps[k]; c->stats.secondaries[k] = h.created[k]; }
     c->stats.generations = h.generations;
     c->stats.overflow = h.overflow;
-    rc = collect_outgoing(c, h, b, &stop_rc);
+    size_t n_out = 0;
+    rc = start_outgoing(c, h, b, &n_out);
     if (rc) return rc;
-    const uint32_t nd = h.done_count[b];
-    done.assign(c->h_done[b], c->h_done[b] + std::min(nd, kDoneChunk));
-    if (nd > kDoneChunk) {  // list b is not rewritten before buffer b is queued again
-      done.resize(nd);
-      CK(cudaMemcpy(done.data() + kDoneChunk, c->P.evt.done_list[b] + kDoneChunk, sizeof(uint32_t) * (nd - kDoneChunk),
-                    cudaMemcpyDeviceToHost));
-    }
-    for (uint32_t s : done) {
-      Request* r;
-      {
-        std::lock_guard<std::mutex> lk(c->mu);
-        auto it = c->reqs.find(c->slot_req[s]);
-        if (it == c->reqs.end()) continue;
-        r = it->second.get();
-      }
-      if (r->state == 1 && r->remaining > 0 && --r->remaining == 0) {
-        rc = complete(c, r, b);
-        if (rc) return rc;
-      }
-    }
+    const uint32_t nd = std::min<uint32_t>(h.done_count[b], (uint32_t)c->slot_req.size());
+    done.assign(c->h_done[b], c->h_done[b] + nd);
     const uint32_t live = h.count[h.gen % 3][0].n + h.count[h.gen % 3][1].n + h.count[h.gen % 3][2].n;
     c->last_live = live;
     c->admit_seen = c->admit_mark[b];
     c->peak_live = live ? std::max<uint64_t>(c->peak_live, live) : 0;
+    // While tracks are live and no request waits for admission, relaunch buffer b at once, so
+    // that the host's processing of this status (outgoing particles, finished events) overlaps
+    // the next chunk instead of delaying the launch of the one after it: on the 10 GeV showers
+    // it took up to 0.5 ms, longer than the short chunks near the end. The relaunched chunk's
+    // outgoing-ring floor counts this chunk's records as read, so it waits for their copy.
+    // With requests waiting, completions free their slots first and the launch follows the
+    // admission at the top of the loop.
+    bool early = false;
+    if (stop_rc == ADEPT_OK && live > 0) {
+      std::lock_guard<std::mutex> lk(c->mu);
+      early = c->pending.empty();
+    }
+    if (early) {
+      if (n_out) CK(cudaStreamWaitEvent(c->stream, c->out_ev, 0));
+      rc = launch_chunk(c, b);
+      if (rc) return rc;
+      queued[b] = true;
+    }
+    rc = finish_outgoing(c, h, n_out, &stop_rc);
+    if (rc) return rc;
+    // the finished events: each slot's request directly, under one lock for the whole list
+    // (a lookup and a lock per slot took longer than the next chunk ran once thousands of
+    // events finished in one chunk, and the GPU waited for the chunk after it)
+    finished.clear();
+    {
+      std::lock_guard<std::mutex> lk(c->mu);
+      for (uint32_t s : done) {
+        Request* r = s < c->slot_req.size() ? c->slot_req[s] : nullptr;
+        if (r && r->state == 1 && r->remaining > 0 && --r->remaining == 0) finished.push_back(r);
+      }
+    }
+    for (Request* r : finished) {
+      rc = complete(c, r);
+      if (rc) return rc;
+    }
     idle_chunks = (live == 0 && done.empty()) ? idle_chunks + 1 : 0;
     if (idle_chunks > 8) {
       std::lock_guard<std::mutex> lk(c->mu);
@@ -1479,9 +1534,11 @@ extern "C" void adept_destroy(adept_ctx* c) {
     if (c->status_ev[b]) cudaEventDestroy(c->status_ev[b]);
   }
   if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+  if (c->out_ev) cudaEventDestroy(c->out_ev);
   if (c->copy_stream) { cudaStreamSynchronize(c->copy_stream); cudaStreamDestroy(c->copy_stream); }
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->h_sub) cudaFreeHost(c->h_sub);
+  if (c->h_leak) cudaFreeHost(c->h_leak);
   for (double* p : c->pool_all) cudaFreeHost(p);
   delete c;
 }

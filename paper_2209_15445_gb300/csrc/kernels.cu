@@ -228,17 +228,22 @@ cudaError_t launch_transport(const Params& P, uint32_t gk, int precision, int sp
 }
 
 // ======================================================================== admission
+// The request's deposit rows are one contiguous range of slots, zeroed by a grid-stride loop
+// over its doubles (coalesced; a row per thread wrote 32 rows per warp store).
 __global__ void k_admit(Params P, uint32_t slot_base, const uint32_t* keys, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const uint32_t s = slot_base + j;
-  P.evt.key[s] = keys[j];
-  P.evt.state[s] = 1u;
-  P.evt.alive[s] = 0xFFFFFFFFu;
-  P.evt.leaked[s] = 0.0;
-  P.evt.killed[s] = 0.0;
-  double* row = P.evt.edep + (size_t)s * P.geo.n_bins;
-  for (int b = 0; b < P.geo.n_bins; ++b) row[b] = 0.0;
+  if (j < n) {
+    const uint32_t s = slot_base + j;
+    P.evt.key[s] = keys[j];
+    P.evt.state[s] = 1u;
+    P.evt.alive[s] = 0xFFFFFFFFu;
+    P.evt.leaked[s] = 0.0;
+    P.evt.killed[s] = 0.0;
+  }
+  double* rows = P.evt.edep + (size_t)slot_base * P.geo.n_bins;
+  const size_t m = (size_t)n * P.geo.n_bins;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
+    rows[i] = 0.0;
 }
 
 cudaError_t launch_admit(const Params& P, uint32_t slot_base, const uint32_t* keys, int n, cudaStream_t st) {
@@ -319,18 +324,16 @@ __global__ void k_mark(Params P) {
   }
 }
 
-// The done list goes to device memory and, for its first kDoneChunk entries, straight to the
-// host's pinned copy of buffer b; the last block to end then writes the whole Ctrl there. The
-// host reads both once the chunk has ended, and no copy runs between two chunks (two
-// device-to-host copies and one host-to-device copy a chunk boundary before).
+// The done list (at most one entry per event slot) goes straight to the host's pinned copy of
+// buffer b; the last block to end then writes the whole Ctrl there. The host reads both once
+// the chunk has ended, and no copy runs between two chunks (two device-to-host copies and one
+// host-to-device copy a chunk boundary before, and a synchronous one for long lists).
 __global__ void k_finish(Params P, int b) {
   const uint32_t gen = __ldcg(&P.ctrl->gen);
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < P.evt.max_slots; s += gridDim.x * blockDim.x) {
     if (P.evt.state[s] == 1u && P.evt.alive[s] != gen) {
       P.evt.state[s] = 2u;
-      const uint32_t k = atomicAdd(&P.ctrl->done_count[b], 1u);
-      P.evt.done_list[b][k] = s;
-      if (k < kDoneChunk) P.h_done[b][k] = s;
+      P.h_done[b][atomicAdd(&P.ctrl->done_count[b], 1u)] = s;
     }
   }
   __shared__ bool last;

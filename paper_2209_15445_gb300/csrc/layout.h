@@ -118,7 +118,6 @@ struct EventView {
   double* edep;        // [slot][n_bins]
   double* leaked;      // [slot]
   double* killed;      // [slot]
-  uint32_t* done_list[2]; // slots found finished, one list per chunk buffer
   uint32_t max_slots;
 };
 
@@ -146,13 +145,12 @@ struct Params {
   double delta_int;     // intersection accuracy, mm
   uint32_t tail_exit;   // a tail chunk ends once this many tracks are live
   // the host's pinned, device-mapped status of the two chunk buffers: the copy of Ctrl and the
-  // first kDoneChunk entries of the done list that a chunk's finish pass writes, and the
+  // done list ([evt.max_slots]: slots found finished) that a chunk's finish pass writes, and the
   // outgoing-ring read position its first kernel reads (so no copy sits between two chunks)
   Ctrl* h_ctrl[2];
   uint32_t* h_done[2];
   const unsigned long long* h_floor[2];
 };
-constexpr uint32_t kDoneChunk = 4096;  // done-list entries written to the host with each status
 
 // device view of one submitted particle; same layout as adept_track in adept.h
 struct TrackIn {
