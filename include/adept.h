@@ -250,9 +250,9 @@ int adept_submit(adept_ctx* ctx, const adept_track* host_tracks, size_t n, uint3
 
 /* Same, but the tracks are already in device memory (n records laid out as
  * adept_track) -- used to time transport with inputs resident in HBM. The records must be
- * written when the call is made (the library reads their event, pdg and energy fields on
- * a stream of its own) and must stay in place until the request has been admitted, which
- * happens at the start of a later adept_transport. Thread-safe. */
+ * written when the call is made (the library copies them back once, on a stream of its
+ * own, for their event, pdg and energy fields) and must stay in place until the request has
+ * been admitted, which happens at the start of a later adept_transport. Thread-safe. */
 int adept_submit_device(adept_ctx* ctx, const void* dev_tracks, size_t n, uint32_t* request_id);
 
 /* Run the stepping loop until every submitted request (including requests submitted
