@@ -324,6 +324,48 @@ __global__ void k_mark(Params P) {
   }
 }
 
+// The same marks with per-block deduplication: a block sets one bit per event slot seen among
+// its share of the live tracks in a shared-memory bitmap, then writes the marks of the slots
+// it saw in slot order (coalesced). All live tracks writing their event's mark, about ten
+// thousand events on a few hundred L2 lines, was bound by the contention on those lines.
+// Used while the bitmap fits 48 KB (evt.max_slots up to 393,216); with few live tracks, whose
+// marks contend little, it marks directly (the bitmap's zeroing and scan cost the one-shower
+// batches 4 us a chunk).
+constexpr uint32_t kMarkBitsMaxSlots = 48u * 1024u * 8u;
+constexpr uint32_t kMarkDirectTracks = 16384u;  // below this many live tracks, no bitmap
+__global__ void k_mark_bits(Params P) {
+  extern __shared__ uint32_t seen[];  // [ceil(max_slots / 32)]
+  const uint32_t gen = __ldcg(&P.ctrl->gen);
+  const int p = gen & 1, cr = gen % 3;
+  const uint32_t n0 = min(__ldcg(&P.ctrl->count[cr][0].n), P.cap), n1 = min(__ldcg(&P.ctrl->count[cr][1].n), P.cap),
+                 n2 = min(__ldcg(&P.ctrl->count[cr][2].n), P.cap);
+  const uint32_t total = n0 + n1 + n2;
+  if (blockIdx.x * blockDim.x >= total) return;  // a block with no tracks has nothing to mark
+  if (total <= kMarkDirectTracks) {  // few tracks contend little: mark directly, as k_mark does
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+      const int sp = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);
+      const uint32_t j = sp == 0 ? i : (sp == 1 ? i - n0 : i - n0 - n1);
+      const TrackSoA& q = P.q[p][sp];
+      const uint32_t ev = q.meta ? q.meta[j].z : q.ev[j];
+      if (P.evt.alive[ev] != gen) P.evt.alive[ev] = gen;
+    }
+    return;
+  }
+  const uint32_t nw = (P.evt.max_slots + 31u) / 32u;
+  for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x) seen[w] = 0u;
+  __syncthreads();
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int sp = i < n0 ? 0 : (i < n0 + n1 ? 1 : 2);
+    const uint32_t j = sp == 0 ? i : (sp == 1 ? i - n0 : i - n0 - n1);
+    const TrackSoA& q = P.q[p][sp];
+    const uint32_t ev = q.meta ? q.meta[j].z : q.ev[j];
+    if (ev < P.evt.max_slots) atomicOr(&seen[ev >> 5], 1u << (ev & 31u));
+  }
+  __syncthreads();
+  for (uint32_t s = threadIdx.x; s < P.evt.max_slots; s += blockDim.x)
+    if ((seen[s >> 5] >> (s & 31u)) & 1u) P.evt.alive[s] = gen;
+}
+
 // The done list (at most one entry per event slot) goes straight to the host's pinned copy of
 // buffer b; the last block to end then writes the whole Ctrl there. The host reads both once
 // the chunk has ended, and no copy runs between two chunks (two device-to-host copies and one
@@ -393,7 +435,10 @@ cudaError_t launch_tail_step(const Params& P, cudaGraphConditionalHandle h, uint
 
 cudaError_t launch_finish(const Params& P, int b, uint32_t gens, cudaStream_t st) {
   k_end_chunk<<<1, 32, 0, st>>>(P, gens);
-  k_mark<<<1216, 256, 0, st>>>(P);
+  if (P.evt.max_slots <= kMarkBitsMaxSlots)
+    k_mark_bits<<<304, 512, sizeof(uint32_t) * ((P.evt.max_slots + 31) / 32), st>>>(P);
+  else
+    k_mark<<<1216, 256, 0, st>>>(P);
   k_finish<<<(P.evt.max_slots + 255) / 256 < 1216 ? (P.evt.max_slots + 255) / 256 : 1216, 256, 0, st>>>(P, b);
   return cudaGetLastError();
 }
