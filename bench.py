@@ -44,8 +44,8 @@ TRACK_BYTES_SPLIT = 64  # x,y,z f64 + direction 3 f32 + E f64 + id u64 + event, 
 # the ncu captures of generation 60 (profiles/transport_kernels_10gev_e_showers_gen60_full.md
 # for the split form, profiles/transport_kernels_10gev_e_showers_fp64_gen60_full.md for the
 # plain FP64 form); valid while the kernel sources hash to NCU_SRC_HASH, null otherwise
-NCU_BYTES_PER_STEP = {1: 108.0, 0: 132.1}
-NCU_SRC_HASH = "74c2415aba673a1c"
+NCU_BYTES_PER_STEP = {1: 107.9, 0: 132.1}
+NCU_SRC_HASH = "0364c2f2c0239b1f"
 
 
 def kernel_src_hash() -> str:
