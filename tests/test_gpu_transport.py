@@ -274,6 +274,38 @@ def test_alone_equals_in_mix():
     tr.close()
 
 
+def test_event_marking_paths_agree_and_a_result_buffer_is_reused():
+    """At a chunk's end the events that still have tracks are marked through a per-block
+    bitmap of the event slots (up to 393,216 slots, with a direct pass below 16,384 live
+    tracks) or, with more slots, by every live track marking its event: both report the same
+    finished events, so the requests' deposits agree (up to the order of the FP64 atomics).
+    A caller's buffer passed to result() is filled in place, also when reused."""
+    need_gpu()
+    geom = W.slab_calorimeter()
+    n = 2000
+    prim = W.electrons(n, 1e4)
+    res = []
+    for slots in (65536, 400000):
+        tr = make(geom, precision=1, arena_bytes=2 << 30, max_events=slots)
+        edep, meta = gpu_run(tr, prim)
+        buf = np.full((n, tr.n_bins), np.nan)
+        for _ in range(2):
+            rid = tr.submit(prim)
+            tr.transport()
+            again, m2 = tr.result(rid, n, out=buf)
+            assert again is buf
+            np.testing.assert_allclose(again, edep, rtol=1e-12, atol=1e-9)
+            assert m2.n_events == n and abs(m2.deposited_MeV - meta.deposited_MeV) <= 1e-9 * meta.deposited_MeV
+        res.append((edep, meta))
+        tr.close()
+    (e0, m0), (e1, m1) = res
+    np.testing.assert_allclose(e1, e0, rtol=1e-12, atol=1e-9)
+    for f in ("deposited_MeV", "leaked_MeV", "killed_MeV"):
+        assert abs(getattr(m1, f) - getattr(m0, f)) <= 1e-9 * max(1.0, abs(getattr(m0, f)))
+    E0 = primary_energy(prim).sum()
+    assert abs(m0.deposited_MeV + m0.leaked_MeV + m0.killed_MeV - E0) <= 1e-9 * E0
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_secondary_counts_and_step_lengths(precision):
     """Secondaries per species and the step-length distribution per species against the
