@@ -1063,8 +1063,9 @@ static int complete(adept_ctx* c, Request* r) {
 }
 
 // The host keeps at most two chunks queued: while chunk b runs, chunk b^1 is already
-// behind it in the stream, so the GPU does not idle while the host reads b's status.
-// A speculative chunk that finds empty queues costs only empty launches.
+// behind it in the stream, so the GPU does not idle while the host reads b's status; once b
+// has ended, its buffer is relaunched before the host processes that status (below). A
+// speculative chunk that finds empty queues costs only empty launches.
 extern "C" int adept_transport(adept_ctx* c, uint64_t timeout_us) {
   if (!c) return ADEPT_EINVAL;
   if (!c->built) return fail(c, ADEPT_ESTATE, "adept_build_tables has not run");
