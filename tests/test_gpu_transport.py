@@ -274,6 +274,40 @@ def test_alone_equals_in_mix():
     tr.close()
 
 
+def test_interleaved_events_number_like_grouped_ones():
+    """A request's events are numbered in the order they first appear and its tracks in the
+    order they come within their event, whether an event's tracks are together or spread
+    through the request (the host's event table, with scattered event numbers that collide in
+    it): the same primaries give the same per-event deposits either way."""
+    need_gpu()
+    geom = W.slab_calorimeter()
+    n_ev, per = 50, 3
+    events = (1000003 + 7919 * np.arange(n_ev) * np.arange(1, n_ev + 1)).astype(np.uint32)
+    kind = [(11, 1000.0), (22, 500.0), (-11, 200.0)]
+    def prim(order):
+        idx = [(k, j) for k in range(n_ev) for j in range(per)] if order == "grouped" else \
+              [(k, j) for j in range(per) for k in range(n_ev)]
+        pdg = np.array([kind[j][0] for k, j in idx], np.int32)
+        E = np.array([kind[j][1] for k, j in idx])
+        pos = np.zeros((len(idx), 3))
+        d = np.tile([0.0, 0.0, 1.0], (len(idx), 1))
+        return W.Primaries(pdg, E, pos, d, np.array([events[k] for k, j in idx], np.uint32))
+    tr = make(geom, precision=1, arena_bytes=1 << 30)
+    res = {}
+    for order in ("grouped", "interleaved"):
+        p = prim(order)
+        rid = tr.submit(p)
+        tr.transport()
+        res[order] = tr.result(rid, n_ev)
+        assert res[order][1].n_events == n_ev
+    tr.close()
+    (g, mg), (i, mi) = res["grouped"], res["interleaved"]
+    np.testing.assert_allclose(i, g, rtol=1e-12, atol=1e-9)
+    E0 = n_ev * sum(E + (2 * ME if pdg == -11 else 0.0) for pdg, E in kind)
+    for m in (mg, mi):
+        assert abs(m.deposited_MeV + m.leaked_MeV + m.killed_MeV - E0) <= 1e-9 * E0
+
+
 def test_event_marking_paths_agree_and_a_result_buffer_is_reused():
     """At a chunk's end the events that still have tracks are marked through a per-block
     bitmap of the event slots (up to 393,216 slots, with a direct pass below 16,384 live
