@@ -15,6 +15,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -1188,6 +1189,23 @@ extern "C" int adept_wait(adept_ctx* c, uint32_t id, uint64_t timeout_us) {
   return c->reqs.count(id) ? ADEPT_OK : ADEPT_ENOTFOUND;
 }
 
+// copy s[lo, hi) to d[lo, hi) and return its sum, with eight partial sums
+static double copy_sum(const double* s, double* d, size_t lo, size_t hi) {
+  double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  size_t i = lo;
+  for (; i + 8 <= hi; i += 8)
+    for (int j = 0; j < 8; ++j) {
+      const double v = s[i + j];
+      d[i + j] = v;
+      a[j] += v;
+    }
+  for (; i < hi; ++i) {
+    d[i] = s[i];
+    a[0] += s[i];
+  }
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
 extern "C" int adept_get_scoring(adept_ctx* c, uint32_t id, double* edep_out, size_t n, adept_result* meta) {
   if (!c) return ADEPT_EINVAL;
   std::unique_ptr<Request> r;
@@ -1202,24 +1220,32 @@ extern "C" int adept_get_scoring(adept_ctx* c, uint32_t id, double* edep_out, si
     c->reqs.erase(it);
   }
   // copy the rows out and sum them in one pass, with eight partial sums (one dependent chain
-  // of 10^6 additions took about a millisecond)
+  // of 10^6 additions took about a millisecond); a large request in up to four parts on as
+  // many threads (one pass over 8 MB took 0.5 ms of a 36 ms headline step on one core). The
+  // parts depend only on the request's size and their sums combine in a fixed order, so the
+  // result does not depend on how many threads could be started.
   const size_t nk = r->keys.size(), m = nk * (size_t)c->n_bins;
   double d = 0, l = 0, k = 0;
   if (nk) {
     const double* s = r->res.p;
-    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    size_t i = 0;
-    for (; i + 8 <= m; i += 8)
-      for (int j = 0; j < 8; ++j) {
-        const double v = s[i + j];
-        edep_out[i + j] = v;
-        a[j] += v;
+    constexpr size_t kPart = (size_t)1 << 17;  // doubles (1 MB) a part at least
+    const size_t np = std::min<size_t>(4, std::max<size_t>(1, m / kPart));
+    const size_t step = (m + np - 1) / np;
+    double part[4] = {0, 0, 0, 0};
+    auto run = [&](size_t t) { part[t] = copy_sum(s, edep_out, std::min(m, t * step), std::min(m, (t + 1) * step)); };
+    std::thread th[3];
+    size_t started = 0;
+    try {
+      for (size_t t = 1; t < np; ++t) {
+        th[t - 1] = std::thread(run, t);
+        ++started;
       }
-    for (; i < m; ++i) {
-      edep_out[i] = s[i];
-      a[0] += s[i];
+    } catch (...) {  // no thread to spare: the parts not started run here
     }
-    d = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    run(0);
+    for (size_t t = started + 1; t < np; ++t) run(t);
+    for (size_t t = 0; t < started; ++t) th[t].join();
+    d = (part[0] + part[1]) + (part[2] + part[3]);
     for (size_t e = 0; e < nk; ++e) {
       l += s[m + e];
       k += s[m + nk + e];
