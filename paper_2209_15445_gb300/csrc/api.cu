@@ -513,6 +513,9 @@ extern "C" int adept_build_tables(adept_ctx* c) {
 // within their event
 template <class FE, class FP, class FX>
 static int prepare_request(adept_ctx* c, Request& r, FE ev_at, FP pdg_at, FX e_at) {
+  // (before the table below, whose size follows n: it must stay under half full)
+  if (r.n > c->stage_cap)
+    return fail(c, ADEPT_EINVAL, "request of %zu tracks exceeds the staging capacity %zu", r.n, c->stage_cap);
   // event number -> index into r.keys: open addressing in a power-of-two table of at least 2n
   // slots (tv holds index + 1, 0 = empty); consecutive tracks of one event skip the lookup
   int bits = 4;
@@ -552,8 +555,6 @@ static int prepare_request(adept_ctx* c, Request& r, FE ev_at, FP pdg_at, FX e_a
     r.energy += e + (p == -11 ? 2 * 0.51099895 : 0.0);
   }
   if (r.keys.size() > c->opt.max_events) return fail(c, ADEPT_EINVAL, "request has more events than event slots");
-  if (r.n > c->stage_cap)
-    return fail(c, ADEPT_EINVAL, "request of %zu tracks exceeds the staging capacity %zu", r.n, c->stage_cap);
   return ADEPT_OK;
 }
 
